@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the DSMC hot path: particle-steps/s of the 5e7-particle VHS workload
+(argon, omega = 0.81, Kn = 0.1, 2,000 cells x 25,000 particles per cell) on one GB300,
+one JSON line on stdout.
+
+A step is one DSMC time step over every particle: collisions with the symmetric
+moment sample, free flight with the body force and the walls, and the stable cell
+sort (five kernel launches).  The particle state (1.6 GB with its sort buffer) is
+resident in HBM and larger than L2, so no flush is needed between steps.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank advances its own independent
+instance (seed = rank): replicas with no data-path collective; the barrier and the
+max over ranks of the timed region only frame the measurement.
+
+--impl reference times the CPU oracle (the plain C DSMC the GPU path is checked
+against) on the host cores, on the same workload; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2311_14140_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = W.VHS_KN01_50M
+METRIC = "particle-steps/s"
+
+# Algorithmic bytes per launch of each kernel, per particle (N) or per histogram
+# entry (W x n_cells), as stated in the design notes.
+def algorithmic_bytes(kernel: str, N: int, n_cells: int, sort_warps: int) -> float:
+    return {
+        "collide_sample": 24.0 * N,       # vx, vy, vz read and written once
+        "move_count": 32.0 * N,           # y, vx, vy, vz read and written once
+        "scatter": 32.0 * N,              # state read once, written once to the other buffer
+        "scan_hist": 12.0 * sort_warps * n_cells,
+        "cell_offsets": 8.0 * n_cells,
+        "init": 16.0 * N,
+    }.get(kernel, 0.0)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if that summary
+    was taken from the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("sources_sha256") != sources_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+
+
+def sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2311_14140_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline_sample(steps: int = 2) -> dict:
+    """The oracle as it stands on one host core: `steps` steps of the full workload after
+    its initialisation (not timed)."""
+    import oracle
+    w = WORKLOAD
+    s = oracle.OracleSim(omega=w.omega, Kn=w.Kn, F=w.body_force, n_cells=w.n_cells,
+                         ppc=w.ppc, seed=0, sample_start=1, G=w.group_size)
+    t0 = time.perf_counter()
+    s.step(steps)
+    t = time.perf_counter() - t0
+    s.close()
+    return {"value": w.n_particles * steps / t, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the full {w.name} workload "
+                      f"({w.n_particles * steps:.1e} particle-steps) after initialisation, "
+                      "single-threaded C oracle"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    w = WORKLOAD
+    s = oracle.OracleSim(omega=w.omega, Kn=w.Kn, F=w.body_force, n_cells=w.n_cells,
+                         ppc=w.ppc, seed=0, sample_start=1, G=w.group_size)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    t = time.perf_counter() - t0
+    s.close()
+    value = w.n_particles * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(w, args.gpus),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps of the full workload after "
+                                       f"{args.warmup} untimed, single-threaded C oracle"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(w, n_gpus):
+    return {"workload": w.name, "gas": "argon VHS omega=0.81", "Kn": w.Kn,
+            "n_cells": w.n_cells, "ppc": w.ppc, "n_particles_per_gpu": w.n_particles,
+            "body_force": w.body_force, "group_size": w.group_size,
+            "dt_factor": w.dt_factor, "parallelism": f"replicas x{n_gpus}",
+            "l2": "inputs larger than L2 (1.6 GB resident state vs 129 MB L2)"}
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2311_14140_gb300 import Dsmc, _build
+    _build.build()
+    torch.cuda.set_device(local)
+    w = WORKLOAD
+    stream = torch.cuda.current_stream()
+    g = Dsmc(w.Kn, w.n_cells, w.ppc, omega=w.omega, body_force=w.body_force, seed=rank,
+             sample_start=1, group_size=w.group_size, dt_factor=w.dt_factor, profile=True)
+    info = g.info()
+    N = info["n_particles"]
+    g.step(args.warmup)
+    g.sync()
+    g.reset_kernel_times()
+
+    # Device-timed region: K steps, kernel timing events on the launch stream.
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    t_dev = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    kt = g.kernel_times()
+    launches = sum(c for _, c in kt.values())
+    g.sync()
+    g.close()
+    del g
+    torch.cuda.synchronize()
+
+    # End-to-end region through the public API: create from parameters (device init),
+    # K steps each followed by a read of the moment sums into pinned host memory.
+    out = torch.empty((w.n_cells, 13), dtype=torch.float64, pin_memory=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g2 = Dsmc(w.Kn, w.n_cells, w.ppc, omega=w.omega, body_force=w.body_force,
+              seed=1000 + rank, sample_start=1, group_size=w.group_size,
+              dt_factor=w.dt_factor)
+    for _ in range(args.steps):
+        g2.step(1)
+        g2.moments(out)
+    g2.close()
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+
+    value = world * N * args.steps / t_dev
+    peak, peak_kind = peaks()
+    dom = max(kt, key=lambda k: kt[k][0])
+    ms_total, cnt = kt[dom]
+    per_launch_s = ms_total / 1e3 / max(cnt, 1)
+    alg = algorithmic_bytes(dom, N, w.n_cells, info["sort_warps"])
+    achieved = alg / per_launch_s / 1e9
+    kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
+                   "share": v[0] / sum(x[0] for x in kt.values()),
+                   "alg_bytes_per_launch": algorithmic_bytes(k, N, w.n_cells, info["sort_warps"]),
+                   "gbs": (algorithmic_bytes(k, N, w.n_cells, info["sort_warps"]) /
+                           (v[0] / 1e3 / v[1]) / 1e9) if v[1] and v[0] > 0 else None}
+               for k, v in kt.items() if v[1]}
+    result = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(w, world),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(dom), "alg_bytes_per_launch": alg},
+        "effective_step": {"bytes_per_particle_step": 32,
+                           "gbs": 32.0 * N * args.steps / t_dev / 1e9,
+                           "frac": 32.0 * N * args.steps / t_dev / 1e9 / peak},
+        "kernels": kernels,
+        "clocks": clk,
+        "e2e": {"value": world * N * args.steps / t_e2e, "unit": METRIC,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": w.n_cells * 13 * 8,
+                "includes": "handle creation and device initialisation, K steps, a moment "
+                            "read into pinned host memory after every step"},
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * dsmc.h -- C ABI of the GB300 (sm_103a) DSMC library for force-driven rarefied
+ * flow between two parallel plates: the micro model of the Micro-Macro-Surrogate
+ * method of arXiv 2311.14140 ("A DSMC-CFD coupling method using surrogate
+ * modelling for low-speed rarefied gas flows").
+ *
+ * The problem (Sec. 2.1): a monatomic gas between two plates held at a constant
+ * temperature, driven by an external acceleration F parallel to the plates, in
+ * steady, fully developed, one-dimensional flow.  Everything is nondimensional as in
+ * Eq. 5: lengths in the plate gap H (walls at y = 0 and y = 1), speeds in
+ * v0 = sqrt(2 k T0 / m) with T0 the wall temperature, time in H / v0, body force
+ * in v0^2 / H, stress in P0.  The Knudsen number enters through the viscosity,
+ * mu0 v0 / (P0 H) = 2 Kn / sqrt(pi) (Eq. 7 against Eq. 3).  The DSMC method itself
+ * is Bird's, which the paper cites (Sec. 1, Sec. 2) without describing it.
+ *
+ * One time step (a call to dsmc_step advances n of them), in this order:
+ *   1. within each cell, NTC collisions of hard-sphere or VHS molecules in
+ *      consecutive groups of at most `group_size` sorted particles, with the cell
+ *      moments sampled half before and half after the collisions when the step is
+ *      at or past `sample_start`;
+ *   2. free flight of every particle for dt with the body force along x, and fully
+ *      diffuse re-emission at the walls (any number of bounces, up to 64);
+ *   3. a stable counting sort of the particles into cells (ties keep their previous
+ *      order).
+ * Random numbers are Philox4x32-10 keyed on the seed with counters built from
+ * (stream, step, slot, bounce) for the flight and (stream, step, cell, group,
+ * candidate) for collisions, so a run is a deterministic function of its inputs.
+ *
+ * Memory and ownership.  All particle and cell data live on the device.  The
+ * library allocates them with cudaMalloc in dsmc_create and frees them in
+ * dsmc_destroy, or uses a caller-owned device workspace given to dsmc_create_in
+ * (dsmc_workspace_bytes says how large), which it never frees.  Output buffers of
+ * the copy functions are caller-owned; they may be host memory (pageable or pinned)
+ * or device memory.
+ *
+ * Streams and errors.  Work is enqueued on the stream of the options (NULL: the
+ * legacy default stream) and is asynchronous unless a function says it
+ * synchronises.  Every function returns a dsmc_status; dsmc_last_error() gives a
+ * message for the last failure on the calling thread.  Device-side limits (bounce
+ * count, rejection-sampling attempts) never trap: kernels record them in a device
+ * error word, and the next synchronising call returns DSMC_E_DEVICE_LIMIT.
+ * One handle must not be used from two threads at once.
+ */
+#ifndef DSMC_H
+#define DSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DSMC_API __attribute__((visibility("default")))
+#else
+#define DSMC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Gas species.  Only omega enters the nondimensional problem: the Knudsen number
+ * fixes n * sigma (Eq. 7), so mass, d_ref and T_ref are informational and only
+ * checked for sign.  omega is the VHS viscosity index, 0.5 <= omega <= 1
+ * (0.5 = hard sphere). */
+typedef struct dsmc_gas {
+  double mass;  /* kg, > 0 */
+  double d_ref; /* m, > 0 */
+  double omega; /* VHS viscosity index */
+  double T_ref; /* K, > 0 */
+} dsmc_gas;
+
+typedef enum dsmc_status {
+  DSMC_OK = 0,
+  DSMC_E_INVAL = 1,        /* bad argument (message in dsmc_last_error) */
+  DSMC_E_NOMEM = 2,        /* device allocation failed or workspace too small */
+  DSMC_E_CUDA = 3,         /* a CUDA call failed */
+  DSMC_E_DEVICE_LIMIT = 4, /* a kernel hit a bounded loop's limit (error word) */
+  DSMC_E_STATE = 5         /* call not valid in the handle's current state */
+} dsmc_status;
+
+/* Options.  Get the defaults from dsmc_default_options and change fields. */
+typedef struct dsmc_options {
+  double dt_factor;       /* dt = dt_factor / nu, nu = n sigma_ref <g> the equilibrium
+                             collision frequency, <g> = 2 sqrt(2/pi); default 0.2 */
+  double dt;              /* > 0: time step in H / v0, overriding dt_factor (required
+                             when Kn is infinite); default 0 */
+  long long sample_start; /* steps numbered from 1; steps >= sample_start are
+                             sampled; default 0 (every step) */
+  int group_size;         /* collision group G: even, 2 <= G <= 512; default 256 */
+  int collisions;         /* 0 turns collisions off; default 1 */
+  int profile;            /* 1: time every kernel launch with CUDA events (then
+                             dsmc_step synchronises at its end); default 0 */
+  void* stream;           /* cudaStream_t for all work; default NULL */
+} dsmc_options;
+
+/* What the handle computes with: the binary32 values are exactly those the kernels
+ * use. */
+typedef struct dsmc_info {
+  long long n_particles;
+  int n_cells;
+  int ppc;
+  long long step;      /* steps completed */
+  long long n_samples; /* sampled steps in the accumulators */
+  double Kn, omega, body_force;
+  double nsigma;       /* n sigma_ref H (Eq. 7 with the VHS viscosity) */
+  double dt;           /* binary64 time step */
+  float dt_f, F_f;     /* binary32 time step and body force */
+  float coef;          /* n sigma_ref dt / (2 ppc): NTC candidate factor */
+  float cvhs, vexp;    /* sigma g / sigma_ref = cvhs * g^vexp (HS: 1, 1) */
+  float smax0;         /* initial (sigma g)_max / sigma_ref */
+  size_t device_bytes; /* device memory the handle uses */
+  int sort_warps;      /* partition of the sort passes */
+  int sort_span;       /* particles per partition */
+} dsmc_info;
+
+typedef struct dsmc_sim* dsmc_handle;
+
+/* Number of raw moment sums per cell returned by dsmc_sample_moments. */
+#define DSMC_NMOM 13
+
+DSMC_API dsmc_status dsmc_default_options(dsmc_options* opt);
+
+/* Device bytes dsmc_create_in needs for n_cells * ppc particles. */
+DSMC_API size_t dsmc_workspace_bytes(int n_cells, int ppc);
+
+/* Create a run: n_cells cells of width 1/n_cells across the gap (Sec. 3 uses
+ * Delta y = 0.005), ppc particles per cell at start, each placed uniformly in its
+ * cell with velocity components N(0, 1/2) (the gas at rest at the wall
+ * temperature, Sec. 2.1), then sorted into cells.  Kn > 0 (+INFINITY: collisionless,
+ * then options.dt must be set); wall_T > 0 is the reference temperature T0;
+ * body_force is F = F' H / v0^2 (Eq. 5); 1 <= n_cells <= 51200, ppc >= 1,
+ * n_cells * ppc <= 2^31 - 2^24.  The library allocates the device memory.  Initialisation
+ * is enqueued on the legacy default stream and completed before return. */
+DSMC_API dsmc_status dsmc_create(const dsmc_gas* gas, double Kn, double wall_T,
+                        double body_force, int n_cells, int ppc, uint64_t seed,
+                        dsmc_handle* out);
+
+/* As dsmc_create, with options applied from the start (their stream is used for
+ * initialisation) and the caller's device workspace of workspace_bytes >=
+ * dsmc_workspace_bytes(n_cells, ppc), 256-byte aligned; NULL workspace: the
+ * library allocates.  The library never frees a caller's workspace. */
+DSMC_API dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T,
+                           double body_force, int n_cells, int ppc, uint64_t seed,
+                           const dsmc_options* opt, void* workspace,
+                           size_t workspace_bytes, dsmc_handle* out);
+
+/* Replace the options.  Takes effect for the next step. */
+DSMC_API dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt);
+
+/* Enqueue n_steps >= 0 steps.  Asynchronous (unless profiling); returns an error
+ * latched by an earlier synchronising call, else DSMC_OK. */
+DSMC_API dsmc_status dsmc_step(dsmc_handle h, int n_steps);
+
+/* Wait for the handle's stream and check the device error word. */
+DSMC_API dsmc_status dsmc_sync(dsmc_handle h);
+
+/* Copy the n_cells x DSMC_NMOM raw sums, row-major per cell, into out (binary64):
+ *   [count, vx, vy, vz, vx^2, vy^2, vz^2, vx vy, vx vz, vy vz, vx|v|^2, vy|v|^2, vz|v|^2]
+ * summed over the particles of the cell and the sampled steps, each step counted
+ * half before and half after its collisions.  Velocities in v0.  *n_samples gets
+ * the number of sampled steps.  Synchronises. */
+DSMC_API dsmc_status dsmc_sample_moments(dsmc_handle h, double* out, long long* n_samples);
+
+/* Zero the moment sums and collision counters (enqueued). */
+DSMC_API dsmc_status dsmc_reset_samples(dsmc_handle h);
+
+/* Copy the particle state in cell order (N floats each; any pointer may be NULL to
+ * skip it).  Synchronises. */
+DSMC_API dsmc_status dsmc_copy_state(dsmc_handle h, float* y, float* vx, float* vy, float* vz);
+
+/* Copy cell data: offset[n_cells + 1] (first slot of each cell in the sorted state),
+ * smax[n_cells] ((sigma g)_max / sigma_ref), ncand[n_cells] and nacc[n_cells]
+ * (collision candidates and accepted collisions since the last reset).  Any pointer
+ * may be NULL.  Synchronises. */
+DSMC_API dsmc_status dsmc_copy_cells(dsmc_handle h, int* offset, float* smax,
+                            unsigned long long* ncand, unsigned long long* nacc);
+
+/* Replace the particle state (N floats each, any order, y in [0, 1]; values outside
+ * are moved onto the nearest wall), the per-cell (sigma g)_max (NULL: keep) and the
+ * step counter, then sort into cells.  This restores a checkpoint bit-exactly.
+ * Synchronises. */
+DSMC_API dsmc_status dsmc_load_state(dsmc_handle h, const float* y, const float* vx,
+                            const float* vy, const float* vz, const float* smax,
+                            long long step);
+
+DSMC_API dsmc_status dsmc_get_info(dsmc_handle h, dsmc_info* info);
+
+/* Kernel timing (options.profile = 1).  For kernel id k < dsmc_kernel_count():
+ * total milliseconds and launches since the last dsmc_reset_kernel_times. */
+DSMC_API int dsmc_kernel_count(void);
+DSMC_API const char* dsmc_kernel_name(int k);
+DSMC_API dsmc_status dsmc_kernel_times(dsmc_handle h, double* total_ms, long long* launches);
+DSMC_API dsmc_status dsmc_reset_kernel_times(dsmc_handle h);
+
+/* Release the handle and the device memory it allocated.  NULL is accepted. */
+DSMC_API dsmc_status dsmc_destroy(dsmc_handle h);
+
+DSMC_API const char* dsmc_last_error(void);
+DSMC_API const char* dsmc_status_string(dsmc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSMC_H */

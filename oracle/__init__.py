@@ -103,6 +103,8 @@ def lib() -> ctypes.CDLL:
             L.or_get_moments.restype = c.c_longlong
             L.or_reset_samples.argtypes = [c.c_void_p]
             L.or_reset_samples.restype = None
+            L.or_get_abs_moments.argtypes = [c.c_void_p, c.c_void_p]
+            L.or_get_abs_moments.restype = None
             L.or_ln_array.argtypes = [c.c_void_p, c.c_void_p, c.c_longlong]
             L.or_ln_array.restype = None
             L.or_exp_array.argtypes = [c.c_void_p, c.c_void_p, c.c_longlong]
@@ -256,6 +258,13 @@ class OracleSim:
         out = np.empty((self.n_cells, NMOM), np.float64)
         n = lib().or_get_moments(self.h, _ptr(out))
         return out, int(n)
+
+    def abs_moments(self):
+        """Sums of |product| per cell and moment, for error bounds of other summation
+        orders of the same products."""
+        out = np.empty((self.n_cells, NMOM), np.float64)
+        lib().or_get_abs_moments(self.h, _ptr(out))
+        return out
 
     def reset_samples(self):
         lib().or_reset_samples(self.h)

@@ -105,6 +105,7 @@ OR_EXPORT void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
 #define OR_ERR_NORMAL_ATTEMPTS 1
 #define OR_ERR_BOUNCES 2
 #define OR_ERR_SPHERE_ATTEMPTS 4
+#define OR_ERR_CANDIDATES 8
 
 static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                  uint32_t out[4]) {
@@ -287,7 +288,9 @@ typedef struct {
   float* smax;                 /* (sigma g)_max per cell, units sigma_ref v0 */
   float* smax_obs;
   unsigned long long *ncand, *nacc;
-  double* acc; /* n_cells x 13 raw sums */
+  double* acc;  /* n_cells x 13 raw sums */
+  double* aacc; /* n_cells x 13 sums of absolute values (error bounds of other
+                   summation orders) */
   long long n_samples;
   long long step;
   int err;
@@ -482,6 +485,10 @@ static void collide_group(osim* s, int c, int nc, int gic, int start, int ng) {
   uint32_t w[4];
   draw(s->seed, 0xffffffffu, (uint32_t)c, st, c3, w);
   if (or_u01(w[0]) < frac) M += 1;
+  if (!(mf <= 1.0e7f)) { /* corrupted (sigma g)_max: skip the group, report */
+    M = 0;
+    s->err |= OR_ERR_CANDIDATES;
+  }
   s->ncand[c] += M;
   float* vx = s->vx + start;
   float* vy = s->vy + start;
@@ -537,9 +544,13 @@ static void collide_all(osim* s) {
 static void sample_all(osim* s, double w) {
   for (int c = 0; c < s->n_cells; ++c) {
     double* a = s->acc + (size_t)c * NMOM;
+    double* b = s->aacc + (size_t)c * NMOM;
     for (int k = s->offset[c]; k < s->offset[c + 1]; ++k) {
       float x = s->vx[k], y = s->vy[k], z = s->vz[k];
       float v2 = x * x + y * y + z * z;
+      float pr[NMOM] = {1.0f, x, y, z, x * x, y * y, z * z, x * y, x * z, y * z,
+                        x * v2, y * v2, z * v2};
+      for (int m = 0; m < NMOM; ++m) b[m] += w * fabs((double)pr[m]);
       a[0] += w;
       a[1] += w * (double)x;
       a[2] += w * (double)y;
@@ -573,7 +584,7 @@ OR_EXPORT void or_destroy(osim* s) {
   free(s->y); free(s->vx); free(s->vy); free(s->vz);
   free(s->ty); free(s->tvx); free(s->tvy); free(s->tvz);
   free(s->cell); free(s->offset); free(s->smax); free(s->smax_obs);
-  free(s->ncand); free(s->nacc); free(s->acc);
+  free(s->ncand); free(s->nacc); free(s->acc); free(s->aacc);
   free(s);
 }
 
@@ -621,6 +632,7 @@ OR_EXPORT osim* or_create(double omega, double Kn, double F, int n_cells, int pp
   s->ncand = calloc((size_t)n_cells, sizeof(unsigned long long));
   s->nacc = calloc((size_t)n_cells, sizeof(unsigned long long));
   s->acc = calloc((size_t)n_cells * NMOM, sizeof(double));
+  s->aacc = calloc((size_t)n_cells * NMOM, sizeof(double));
   for (int c = 0; c < n_cells; ++c) s->smax[c] = s->smax0;
   init_particles(s);
   index_cells(s);
@@ -678,8 +690,13 @@ OR_EXPORT long long or_get_moments(const osim* s, double* out) {
   return s->n_samples;
 }
 
+OR_EXPORT void or_get_abs_moments(const osim* s, double* out) {
+  memcpy(out, s->aacc, sizeof(double) * (size_t)s->n_cells * NMOM);
+}
+
 OR_EXPORT void or_reset_samples(osim* s) {
   memset(s->acc, 0, sizeof(double) * (size_t)s->n_cells * NMOM);
+  memset(s->aacc, 0, sizeof(double) * (size_t)s->n_cells * NMOM);
   memset(s->ncand, 0, 8 * (size_t)s->n_cells);
   memset(s->nacc, 0, 8 * (size_t)s->n_cells);
   s->n_samples = 0;

@@ -1,0 +1,147 @@
+// dsmc_device.cuh -- device arithmetic shared by the DSMC kernels: the Philox
+// generator, the uniform and Gaussian maps, the binary32 logarithm and exponential,
+// and the cell index.  Every floating-point operation that decides a trajectory is
+// written with an explicit round-to-nearest intrinsic (__fmul_rn, __fadd_rn, ...)
+// so that no contraction into FMA can happen, whatever the compile flags: a run is
+// then a deterministic function of its inputs, operation for operation.
+#pragma once
+
+#include <stdint.h>
+
+#include "dsmc_internal.h"
+
+namespace dsmc {
+
+// Random-number streams: the top byte of the last counter word.
+constexpr uint32_t kStreamInit = 1u;
+constexpr uint32_t kStreamMove = 2u;
+constexpr uint32_t kStreamColl = 3u;
+
+constexpr int kNormalAttempts = 30;  // sub-draws 1..15, two attempts per draw
+constexpr int kMaxBounces = 64;
+
+
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds; round r uses the key plus r
+// Weyl increments.  The two 32x32 products give hi/lo halves.
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Uniform in (0,1) from the top 23 bits: (m + 1/2) 2^-23, exact in binary32.
+__device__ __forceinline__ float u01(uint32_t x) {
+  return fmul(fadd((float)(x >> 9), 0.5f), 0x1p-23f);
+}
+
+// Uniform in (-1,1), never 0: 2u - 1 (exact).
+__device__ __forceinline__ float s11(uint32_t x) { return fsub(fmul(2.0f, u01(x)), 1.0f); }
+
+// ln x for finite x > 0: x = m 2^e with m in [sqrt(1/2), sqrt(2)];
+// ln m = 2 artanh(s), s = (m-1)/(m+1), by its odd power series through s^9;
+// ln 2 as a 17-bit head (e * head exact) plus a tail.
+__device__ __forceinline__ float ln32(float x) {
+  uint32_t b = __float_as_uint(x);
+  int e = 0;
+  if (b < 0x00800000u) {
+    b = __float_as_uint(fmul(x, 0x1p24f));
+    e = -24;
+  }
+  e += (int)(b >> 23) - 127;
+  float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) {
+    m = fmul(m, 0.5f);
+    e += 1;
+  }
+  const float f = fsub(m, 1.0f);
+  const float s = fdiv(f, fadd(2.0f, f));
+  const float z = fmul(s, s);
+  float p = fmul(0x1.c71c72p-4f, z);  // z/9
+  p = fmul(fadd(p, 0x1.24924ap-3f), z);
+  p = fmul(fadd(p, 0x1.99999ap-3f), z);
+  p = fmul(fadd(p, 0x1.555556p-2f), z);
+  const float t = fadd(fmul(s, p), s);
+  const float lnm = fadd(t, t);
+  const float ef = (float)e;
+  return fadd(fadd(fmul(ef, 0x1.7f7d1cp-20f), lnm), fmul(ef, 0x1.62e4p-1f));
+}
+
+// e^x: x = k ln2 + r, k = floor(x / ln2 + 1/2); Taylor polynomial of e^r through
+// r^7 (Horner); scale by 2^k through the exponent field.  0 below -87.
+__device__ __forceinline__ float exp32(float x) {
+  if (x < -87.0f) return 0.0f;
+  if (x > 88.0f) x = 88.0f;
+  const float kf = floorf(fadd(fmul(x, 0x1.715476p+0f), 0.5f));
+  float r = fsub(x, fmul(kf, 0x1.62e4p-1f));
+  r = fsub(r, fmul(kf, 0x1.7f7d1cp-20f));
+  float p = fmul(0x1.a01a02p-13f, r);
+  p = fmul(fadd(p, 0x1.6c16c2p-10f), r);
+  p = fmul(fadd(p, 0x1.111112p-7f), r);
+  p = fmul(fadd(p, 0x1.555556p-5f), r);
+  p = fmul(fadd(p, 0x1.555556p-3f), r);
+  p = fmul(fadd(p, 0.5f), r);
+  p = fmul(fadd(p, 1.0f), r);
+  p = fadd(p, 1.0f);
+  const int k = (int)kf;
+  return fmul(p, __uint_as_float((uint32_t)(k + 127) << 23));
+}
+
+// g^a for g >= 0 (0 at g = 0).
+__device__ __forceinline__ float pow32(float g, float a) {
+  if (g == 0.0f) return 0.0f;
+  return exp32(fmul(a, ln32(g)));
+}
+
+// One polar (Marsaglia-Bray) attempt: two N(0,1/2) deviates or a rejection.
+__device__ __forceinline__ bool polar_pair(uint32_t w0, uint32_t w1, float& z0, float& z1) {
+  const float a0 = s11(w0);
+  const float a1 = s11(w1);
+  const float s = fadd(fmul(a0, a0), fmul(a1, a1));
+  if (s >= 1.0f) return false;
+  const float fac = fsqrt(fdiv(-ln32(s), s));
+  z0 = fmul(a0, fac);
+  z1 = fmul(a1, fac);
+  return true;
+}
+
+// Cell of y in [0,1]: truncation of y * n_cells, clamped to the last cell.
+__device__ __forceinline__ int cell_of(float y, int n_cells, float ncf) {
+  int c = (int)fmul(y, ncf);
+  c = c < n_cells ? c : n_cells - 1;
+  return c > 0 ? c : 0;
+}
+
+// Groups of a cell with nc particles (runs of G; a remainder below G/2 joins the
+// previous run).
+__device__ __forceinline__ int group_count(int nc, int G) {
+  int ng = nc / G;
+  const int r = nc - ng * G;
+  if (r > 0 && (ng == 0 || r >= G / 2)) ng += 1;
+  return ng;
+}
+
+}  // namespace dsmc

@@ -1,0 +1,288 @@
+"""ctypes binding of the sm_103a DSMC library (``include/dsmc.h``).
+
+Argument marshalling only: every step of the DSMC runs in the library's CUDA
+kernels.  PyTorch, when present, provides the device workspace (a uint8 tensor) and
+the CUDA stream (the current stream); without it the library allocates its own
+memory and uses the legacy default stream.  There is no CPU path: if the library is
+missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdsmc.so")
+NMOM = 13
+
+DSMC_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
+          4: "device limit reached", 5: "invalid state"}
+
+
+class DsmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Gas(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("d_ref", ctypes.c_double),
+                ("omega", ctypes.c_double), ("T_ref", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("dt_factor", ctypes.c_double), ("dt", ctypes.c_double),
+                ("sample_start", ctypes.c_longlong), ("group_size", ctypes.c_int),
+                ("collisions", ctypes.c_int), ("profile", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_longlong), ("n_cells", ctypes.c_int),
+                ("ppc", ctypes.c_int), ("step", ctypes.c_longlong),
+                ("n_samples", ctypes.c_longlong), ("Kn", ctypes.c_double),
+                ("omega", ctypes.c_double), ("body_force", ctypes.c_double),
+                ("nsigma", ctypes.c_double), ("dt", ctypes.c_double),
+                ("dt_f", ctypes.c_float), ("F_f", ctypes.c_float), ("coef", ctypes.c_float),
+                ("cvhs", ctypes.c_float), ("vexp", ctypes.c_float), ("smax0", ctypes.c_float),
+                ("device_bytes", ctypes.c_size_t), ("sort_warps", ctypes.c_int),
+                ("sort_span", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load ``libdsmc.so`` and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(nvcc, sm_103a); there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    c = ctypes
+    H = c.c_void_p
+    st = c.c_int
+    sig = {
+        "dsmc_default_options": (st, [c.POINTER(Options)]),
+        "dsmc_workspace_bytes": (c.c_size_t, [c.c_int, c.c_int]),
+        "dsmc_create": (st, [c.POINTER(Gas), c.c_double, c.c_double, c.c_double, c.c_int,
+                             c.c_int, c.c_uint64, c.POINTER(H)]),
+        "dsmc_create_in": (st, [c.POINTER(Gas), c.c_double, c.c_double, c.c_double, c.c_int,
+                                c.c_int, c.c_uint64, c.POINTER(Options), c.c_void_p,
+                                c.c_size_t, c.POINTER(H)]),
+        "dsmc_set_options": (st, [H, c.POINTER(Options)]),
+        "dsmc_step": (st, [H, c.c_int]),
+        "dsmc_sync": (st, [H]),
+        "dsmc_sample_moments": (st, [H, c.c_void_p, c.POINTER(c.c_longlong)]),
+        "dsmc_reset_samples": (st, [H]),
+        "dsmc_copy_state": (st, [H, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "dsmc_copy_cells": (st, [H, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "dsmc_load_state": (st, [H, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p,
+                                 c.c_void_p, c.c_longlong]),
+        "dsmc_get_info": (st, [H, c.POINTER(Info)]),
+        "dsmc_kernel_count": (c.c_int, []),
+        "dsmc_kernel_name": (c.c_char_p, [c.c_int]),
+        "dsmc_kernel_times": (st, [H, c.c_void_p, c.c_void_p]),
+        "dsmc_reset_kernel_times": (st, [H]),
+        "dsmc_destroy": (st, [H]),
+        "dsmc_last_error": (c.c_char_p, []),
+        "dsmc_status_string": (c.c_char_p, [c.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != DSMC_OK:
+        raise DsmcError(status, load_library().dsmc_last_error().decode())
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a contiguous numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def default_options() -> Options:
+    o = Options()
+    _check(load_library().dsmc_default_options(ctypes.byref(o)))
+    return o
+
+
+# Argon: mass, VHS reference diameter (Bird's table) and reference temperature.
+ARGON = dict(mass=6.63e-26, d_ref=4.17e-10, T_ref=273.0)
+
+
+class Dsmc:
+    """One DSMC run on the current CUDA device (see ``include/dsmc.h``).
+
+    ``workspace``: "torch" (a torch uint8 tensor on the device owns the memory; the
+    current torch stream is used unless ``stream`` is given) or "library" (the
+    library calls cudaMalloc).
+    """
+
+    def __init__(self, Kn: float, n_cells: int, ppc: int, *, omega: float = 0.5,
+                 body_force: float = 0.0, seed: int = 0, wall_T: float = 273.0,
+                 dt_factor: float = 0.2, dt: float = 0.0, sample_start: int = 0,
+                 group_size: int = 256, collisions: bool = True, profile: bool = False,
+                 stream=None, workspace: str = "torch", gas: Optional[dict] = None):
+        L = load_library()
+        self._lib = L
+        self.n_cells, self.ppc = int(n_cells), int(ppc)
+        self.N = self.n_cells * self.ppc
+        g = dict(ARGON)
+        g.update(gas or {})
+        self._gas = Gas(g["mass"], g["d_ref"], float(omega), g["T_ref"])
+        o = default_options()
+        o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
+        o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
+        self._ws = None
+        if workspace == "torch":
+            import torch
+            nbytes = L.dsmc_workspace_bytes(self.n_cells, self.ppc)
+            self._ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+            ws_ptr, ws_bytes = self._ws.data_ptr(), nbytes
+        elif workspace == "library":
+            ws_ptr, ws_bytes = None, 0
+        else:
+            raise ValueError("workspace must be 'torch' or 'library'")
+        o.stream = int(stream) if stream is not None else None
+        self._opt = o
+        h = ctypes.c_void_p()
+        _check(L.dsmc_create_in(ctypes.byref(self._gas), float(Kn), float(wall_T),
+                                float(body_force), self.n_cells, self.ppc,
+                                int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(o), ws_ptr,
+                                ws_bytes, ctypes.byref(h)))
+        self._h = h
+
+    # lifetime -------------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.dsmc_destroy(self._h)
+            self._h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # stepping -------------------------------------------------------------------
+    def step(self, n: int = 1) -> None:
+        _check(self._lib.dsmc_step(self._h, int(n)))
+
+    def sync(self) -> None:
+        _check(self._lib.dsmc_sync(self._h))
+
+    def set_options(self, **kw) -> None:
+        o = Options.from_buffer_copy(self._opt)
+        for k, v in kw.items():
+            if k == "stream":
+                v = int(v) if v is not None else None
+            setattr(o, k, v)
+        _check(self._lib.dsmc_set_options(self._h, ctypes.byref(o)))
+        self._opt = o
+
+    # outputs --------------------------------------------------------------------
+    def moments(self, out=None):
+        """(raw sums [n_cells, 13] float64, sampled steps); ``out`` may be a pinned or
+        device buffer of that shape."""
+        if out is None:
+            out = np.empty((self.n_cells, NMOM), np.float64)
+        ns = ctypes.c_longlong()
+        _check(self._lib.dsmc_sample_moments(self._h, _ptr(out), ctypes.byref(ns)))
+        return out, int(ns.value)
+
+    def reset_samples(self) -> None:
+        _check(self._lib.dsmc_reset_samples(self._h))
+
+    def state(self):
+        arrs = [np.empty(self.N, np.float32) for _ in range(4)]
+        _check(self._lib.dsmc_copy_state(self._h, *[_ptr(a) for a in arrs]))
+        return tuple(arrs)
+
+    def state_into(self, y=None, vx=None, vy=None, vz=None) -> None:
+        _check(self._lib.dsmc_copy_state(self._h, _ptr(y), _ptr(vx), _ptr(vy), _ptr(vz)))
+
+    def cells(self):
+        off = np.empty(self.n_cells + 1, np.int32)
+        smax = np.empty(self.n_cells, np.float32)
+        nc = np.empty(self.n_cells, np.uint64)
+        na = np.empty(self.n_cells, np.uint64)
+        _check(self._lib.dsmc_copy_cells(self._h, _ptr(off), _ptr(smax), _ptr(nc), _ptr(na)))
+        return off, smax, nc, na
+
+    def load_state(self, y, vx, vy, vz, smax=None, step: int = 0) -> None:
+        arrs = [np.ascontiguousarray(a, np.float32) if isinstance(a, np.ndarray) else a
+                for a in (y, vx, vy, vz)]
+        sm = None if smax is None else np.ascontiguousarray(smax, np.float32)
+        _check(self._lib.dsmc_load_state(self._h, *[_ptr(a) for a in arrs], _ptr(sm),
+                                         int(step)))
+
+    def info(self) -> dict:
+        i = Info()
+        _check(self._lib.dsmc_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def kernel_times(self) -> dict:
+        n = self._lib.dsmc_kernel_count()
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.int64)
+        _check(self._lib.dsmc_kernel_times(self._h, _ptr(ms), _ptr(cnt)))
+        return {self._lib.dsmc_kernel_name(k).decode(): (float(ms[k]), int(cnt[k]))
+                for k in range(n)}
+
+    def reset_kernel_times(self) -> None:
+        _check(self._lib.dsmc_reset_kernel_times(self._h))
+
+
+def fields(acc, n_samples: int, ppc: int) -> dict:
+    """Cell fields from raw sums: relative density n, velocity (v0), temperature (T0),
+    shear stress P_xy (P0; rho / P0 = 2 / v0^2 in the units of Eq. 5) and heat flux
+    (P0 v0), from central moments of the sampled velocities."""
+    a = np.asarray(acc, np.float64)
+    cnt = a[:, 0]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mean = a[:, 1:4] / cnt[:, None]
+        second = np.empty((a.shape[0], 3, 3))
+        idx = {(0, 0): 4, (1, 1): 5, (2, 2): 6, (0, 1): 7, (0, 2): 8, (1, 2): 9}
+        for (i, j), k in idx.items():
+            second[:, i, j] = second[:, j, i] = a[:, k] / cnt
+        third = a[:, 10:13] / cnt[:, None]  # <v_i |v|^2>
+        rel_n = cnt / (n_samples * ppc)
+        cov = second - mean[:, :, None] * mean[:, None, :]  # <c_i c_j>
+        csq = np.trace(cov, axis1=1, axis2=2)
+        msq = (mean ** 2).sum(1)
+        vsq = np.trace(second, axis1=1, axis2=2)
+        # <c_i |c|^2> expanded in raw moments
+        q_raw = (third - 2.0 * np.einsum("nij,nj->ni", second, mean)
+                 - mean * vsq[:, None] + 2.0 * mean * msq[:, None])
+    return {"n": rel_n, "ux": mean[:, 0], "uy": mean[:, 1], "uz": mean[:, 2],
+            "T": (2.0 / 3.0) * csq, "Pxy": 2.0 * rel_n * cov[:, 0, 1],
+            "qx": rel_n * q_raw[:, 0], "qy": rel_n * q_raw[:, 1]}
+

@@ -1,0 +1,85 @@
+"""Synthetic workload definitions: parameter sets and seeds only.
+
+These describe the runs (Kn, gas, cells, particles per cell, force, steps, seeds)
+that the tests and the benchmark feed to both the CUDA library and the oracle.  This
+module holds none of the DSMC arithmetic; each side derives its own time step,
+cross-sections and collision parameters from these inputs.
+
+Shapes follow the paper's workloads (Sec. 3: Delta y = 0.005 cells, 50 to 500
+particles per cell, low-speed force-driven flow, long time averages) scaled to the
+sizes of the benchmark configurations below.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+
+def f0_force(Kn: float, sigma_p: float = 1.0) -> float:
+    """Body force (v0^2/H) whose slip-Stokes channel-mean speed is 1e-3 v0: the mean
+    of the Eq. 8 parabola (S = 0) plus first-order slip (Eq. 10),
+    u_mean = sqrt(pi) F / (12 Kn) + sigma_P F, with sigma_P := 1."""
+    return 1e-3 / (math.sqrt(math.pi) / (12.0 * Kn) + sigma_p)
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    omega: float
+    Kn: float
+    n_cells: int
+    ppc: int
+    body_force: float
+    steps: int
+    sample_start: int
+    seeds: tuple = (0,)
+    group_size: int = 256
+    dt_factor: float = 0.2
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_particles(self) -> int:
+        return self.n_cells * self.ppc
+
+
+# Argon hard spheres at Kn = 1: 100 cells, 200 particles per cell, 2,000 steps with the
+# last 1,000 sampled, mean speed ~1e-3 v0.
+HS_KN1 = Workload("hs_kn1_100c_200ppc", omega=0.5, Kn=1.0, n_cells=100, ppc=200,
+                  body_force=f0_force(1.0), steps=2000, sample_start=1001,
+                  seeds=tuple(range(16)))
+
+# Argon VHS (omega = 0.81) at Kn = 0.1: 2,000 cells, 25,000 particles per cell
+# (5e7 particles), 20,000 steps sampled after step 5,000.
+VHS_KN01_50M = Workload("vhs_kn0.1_2000c_25000ppc", omega=0.81, Kn=0.1, n_cells=2000,
+                        ppc=25000, body_force=f0_force(0.1), steps=20000,
+                        sample_start=5001, seeds=(0, 1, 2, 3))
+
+
+def scaled(w: Workload, n_cells: int = None, ppc: int = None, **kw) -> Workload:
+    """The same physics with fewer cells or particles (parity-test sizes)."""
+    d = dict(w.__dict__)
+    d.update(kw)
+    if n_cells is not None:
+        d["n_cells"] = n_cells
+    if ppc is not None:
+        d["ppc"] = ppc
+    d["name"] = f"{w.name}@{d['n_cells']}c_{d['ppc']}ppc"
+    return Workload(**d)
+
+
+def batch_instances(n: int = 256, seed: int = 12345):
+    """Independent runs with Kn log-uniform in [0.05, 10], cells uniform in
+    {50..1000}, particles per cell uniform in {50..400}, force uniform in
+    [0.5, 2] x f0_force(1)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        Kn = float(math.exp(rng.uniform(math.log(0.05), math.log(10.0))))
+        out.append(Workload(f"batch{i}", omega=0.5, Kn=Kn,
+                            n_cells=int(rng.integers(50, 1001)),
+                            ppc=int(rng.integers(50, 401)),
+                            body_force=float(rng.uniform(0.5, 2.0) * f0_force(1.0)),
+                            steps=2000, sample_start=1001,
+                            seeds=(int(rng.integers(0, 2 ** 63 - 1)),)))
+    return out

@@ -1,0 +1,107 @@
+"""The C-ABI library on the CPU side (no GPU needed): it loads, exports every symbol
+that include/dsmc.h declares, and rejects bad arguments before touching the device."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_2311_14140_gb300 import dsmc as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^DSMC_API\s+[\w\s\*]+?\b(dsmc_\w+)\(", text, re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_14140_gb300 import _build
+    _build.build()
+    return D.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = set(_declared())
+    for required in ("dsmc_create", "dsmc_step", "dsmc_sample_moments", "dsmc_destroy"):
+        assert required in names
+    assert len(names) >= 20
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_default_options(lib):
+    o = D.default_options()
+    assert (o.dt_factor, o.dt, o.sample_start, o.group_size, o.collisions, o.profile) == \
+        (0.2, 0.0, 0, 256, 1, 0)
+    assert lib.dsmc_kernel_count() == 6
+    assert lib.dsmc_kernel_name(0) == b"init"
+    assert lib.dsmc_status_string(4) == b"device limit reached"
+
+
+def test_workspace_bytes_grow_with_size(lib):
+    a = lib.dsmc_workspace_bytes(100, 200)
+    b = lib.dsmc_workspace_bytes(2000, 25000)
+    assert 0 < a < b
+    assert b >= 8 * 4 * 2000 * 25000  # two SoA copies of y, vx, vy, vz
+    assert lib.dsmc_workspace_bytes(0, 10) == 0
+
+
+def _create(lib, gas=None, Kn=1.0, wall_T=273.0, F=0.0, n_cells=10, ppc=10, opt=None):
+    g = D.Gas(6.63e-26, 4.17e-10, 0.5, 273.0) if gas is None else gas
+    h = ctypes.c_void_p()
+    o = D.default_options() if opt is None else opt
+    st = lib.dsmc_create_in(ctypes.byref(g), Kn, wall_T, F, n_cells, ppc, 0, ctypes.byref(o),
+                            None, 0, ctypes.byref(h))
+    return st, lib.dsmc_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(Kn=0.0), "Kn"), (dict(Kn=-1.0), "Kn"), (dict(Kn=math.nan), "Kn"),
+    (dict(wall_T=0.0), "wall_T"), (dict(F=math.inf), "body_force"),
+    (dict(n_cells=0), "n_cells"), (dict(ppc=0), "ppc"),
+    (dict(n_cells=70000, ppc=1), "51200"), (dict(n_cells=50000, ppc=50000), "2^31 - 2^24"),
+    (dict(Kn=math.inf), "time step"),
+])
+def test_bad_arguments_are_rejected(lib, kw, needle):
+    st, msg = _create(lib, **kw)
+    assert st == 1 and needle in msg
+
+
+def test_bad_gas_and_options_rejected(lib):
+    st, msg = _create(lib, gas=D.Gas(6.63e-26, 4.17e-10, 0.4, 273.0))
+    assert st == 1 and "omega" in msg
+    st, msg = _create(lib, gas=D.Gas(-1.0, 4.17e-10, 0.5, 273.0))
+    assert st == 1 and "mass" in msg
+    for field, val in (("group_size", 3), ("group_size", 1024), ("dt_factor", 0.0),
+                       ("dt", -1.0)):
+        o = D.default_options()
+        setattr(o, field, val)
+        st, msg = _create(lib, opt=o)
+        assert st == 1 and "options" in msg, (field, msg)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.dsmc_step(None, 1) == 1
+    assert lib.dsmc_sync(None) == 1
+    assert lib.dsmc_destroy(None) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    saved = D._lib
+    try:
+        D._lib = None
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            D.load_library(str(tmp_path / "libdsmc.so"))
+    finally:
+        D._lib = saved
