@@ -102,7 +102,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -192,20 +192,26 @@ def run_reference(args, world, rank):
     w = WORKLOAD
     s = oracle.OracleSim(omega=w.omega, Kn=w.Kn, F=w.body_force, n_cells=w.n_cells,
                          ppc=w.ppc, seed=0, sample_start=1, G=w.group_size)
-    s.step(args.warmup)
+    # One oracle step of the full workload takes seconds on one core: bound the sample
+    # so that the whole run stays within a few minutes.
+    warm = min(args.warmup, 3)
+    timed_steps = min(args.steps, 20)
+    s.step(warm)
     t0 = time.perf_counter()
-    s.step(args.steps)
+    s.step(timed_steps)
     t = time.perf_counter() - t0
     s.close()
-    value = w.n_particles * args.steps / t
+    value = w.n_particles * timed_steps / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "ms_per_step": 1e3 * t / timed_steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(w, args.gpus),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed steps of the full workload after "
-                                       f"{args.warmup} untimed, single-threaded C oracle"},
+                             "sample": f"{timed_steps} timed steps of the full workload after "
+                                       f"{warm} untimed (at most 20 and 3 of the requested "
+                                       f"{args.steps} and {args.warmup}), single-threaded "
+                                       "C oracle"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -316,11 +322,18 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=None,
+                    help="override the cell count (profiling cases only)")
+    ap.add_argument("--ppc", type=int, default=None,
+                    help="override particles per cell (profiling cases only)")
     args = ap.parse_args()
+    global WORKLOAD
+    if args.cells or args.ppc:
+        WORKLOAD = W.scaled(WORKLOAD, n_cells=args.cells, ppc=args.ppc)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
