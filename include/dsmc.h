@@ -194,6 +194,29 @@ DSMC_API dsmc_status dsmc_reset_kernel_times(dsmc_handle h);
 /* Release the handle and the device memory it allocated.  NULL is accepted. */
 DSMC_API dsmc_status dsmc_destroy(dsmc_handle h);
 
+/* Stable sort of a particle state into cells that allocates nothing.  The paper has
+ * no counterpart: this is a service for callers that cannot allocate device memory
+ * when they need the sort, such as plug-ins inside a runtime that owns all device
+ * memory and lends them no allocator, or latency-sensitive loops that must avoid the
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ * Inputs y, vx, vy, vz and outputs y_out, vx_out, vy_out, vz_out (n_particles floats
+ * each) and offset_out (n_cells + 1 ints) are caller-owned device memory; outputs
+ * must not alias inputs.  On return (asynchronously, on `stream`) the outputs hold
+ * the state ordered by cell, cell = trunc(y * n_cells) clamped to [0, n_cells - 1],
+ * particles of one cell in their input order, and offset_out[c] is the first slot of
+ * cell c (offset_out[n_cells] = n_particles), exactly as dsmc_load_state sorts.
+ * Scratch: a fixed 8 MiB array compiled into the library, held by every GPU that
+ * loads it until the process exits.  Calls on one GPU that overlap in time (other
+ * streams or threads) share it and race.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture on the device.  Limits: 1 <= n_cells <= 51200,
+ * 1 <= n_particles <= 2^31 - 2^24; anything else returns DSMC_E_INVAL with a message
+ * in dsmc_last_error().  No cudaMalloc, cudaFree or allocating library call is made. */
+DSMC_API dsmc_status dsmc_sort_cells_static(const float* y, const float* vx, const float* vy,
+                                           const float* vz, float* y_out, float* vx_out,
+                                           float* vy_out, float* vz_out, int* offset_out,
+                                           int n_particles, int n_cells, void* stream);
+
 DSMC_API const char* dsmc_last_error(void);
 DSMC_API const char* dsmc_status_string(dsmc_status s);
 

@@ -156,6 +156,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void dsmc::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct dsmc_sim {
   int device = 0;
   int n_cells = 0, ppc = 0;

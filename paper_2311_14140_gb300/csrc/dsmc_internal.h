@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace dsmc {
 
 constexpr int kNMom = 13;          // raw moment sums per cell
@@ -79,5 +81,8 @@ cudaError_t launch_collide_sample(const DevState& s, int n_cells, const int* off
                                   cudaStream_t st);
 cudaError_t launch_clamp_y(float* y, int N, cudaStream_t st);
 cudaError_t set_kernel_smem_limits(size_t sort_bytes, size_t collide_bytes);
+
+// Sets the message dsmc_last_error() returns on the calling thread.
+void set_last_error(const std::string& msg);
 
 }  // namespace dsmc
