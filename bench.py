@@ -41,11 +41,12 @@ METRIC = "particle-steps/s"
 # entry (W x n_cells), as stated in the design notes.
 def algorithmic_bytes(kernel: str, N: int, n_cells: int, sort_warps: int) -> float:
     return {
-        "collide_sample": 24.0 * N,       # vx, vy, vz read and written once
-        "move_count": 32.0 * N,           # y, vx, vy, vz read and written once
-        "scatter": 32.0 * N,              # state read once, written once to the other buffer
+        "collide_move": 32.0 * N,         # y, vx, vy, vz read and written once, in place
+        "scatter_spans": 32.0 * N,        # state read once, written once to the other buffer
         "scan_hist": 12.0 * sort_warps * n_cells,
         "cell_offsets": 8.0 * n_cells,
+        "index_count": 4.0 * N,
+        "index_scatter": 32.0 * N,
         "init": 16.0 * N,
     }.get(kernel, 0.0)
 
@@ -284,12 +285,12 @@ def run_ours(args, world, rank, local):
     dom = max(kt, key=lambda k: kt[k][0])
     ms_total, cnt = kt[dom]
     per_launch_s = ms_total / 1e3 / max(cnt, 1)
-    alg = algorithmic_bytes(dom, N, w.n_cells, info["sort_warps"])
+    alg = algorithmic_bytes(dom, N, w.n_cells, info["n_spans"])
     achieved = alg / per_launch_s / 1e9
     kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
                    "share": v[0] / sum(x[0] for x in kt.values()),
-                   "alg_bytes_per_launch": algorithmic_bytes(k, N, w.n_cells, info["sort_warps"]),
-                   "gbs": (algorithmic_bytes(k, N, w.n_cells, info["sort_warps"]) /
+                   "alg_bytes_per_launch": algorithmic_bytes(k, N, w.n_cells, info["n_spans"]),
+                   "gbs": (algorithmic_bytes(k, N, w.n_cells, info["n_spans"]) /
                            (v[0] / 1e3 / v[1]) / 1e9) if v[1] and v[0] > 0 else None}
                for k, v in kt.items() if v[1]}
     result = {

@@ -106,10 +106,13 @@ typedef struct dsmc_info {
   float dt_f, F_f;     /* binary32 time step and body force */
   float coef;          /* n sigma_ref dt / (2 ppc): NTC candidate factor */
   float cvhs, vexp;    /* sigma g / sigma_ref = cvhs * g^vexp (HS: 1, 1) */
+  float vinv;          /* 1 / vexp (0 when omega = 1) */
   float smax0;         /* initial (sigma g)_max / sigma_ref */
   size_t device_bytes; /* device memory the handle uses */
-  int sort_warps;      /* partition of the sort passes */
-  int sort_span;       /* particles per partition */
+  int sort_warps;      /* partition of the stand-alone sort into cells */
+  int sort_span;       /* particles per partition of that sort */
+  int cells_per_span;  /* cells per span of the step's two state passes */
+  int n_spans;         /* spans (CTAs of the collide/move pass) */
 } dsmc_info;
 
 typedef struct dsmc_sim* dsmc_handle;
@@ -127,8 +130,9 @@ DSMC_API size_t dsmc_workspace_bytes(int n_cells, int ppc);
  * cell with velocity components N(0, 1/2) (the gas at rest at the wall
  * temperature, Sec. 2.1), then sorted into cells.  Kn > 0 (+INFINITY: collisionless,
  * then options.dt must be set); wall_T > 0 is the reference temperature T0;
- * body_force is F = F' H / v0^2 (Eq. 5); 1 <= n_cells <= 51200, ppc >= 1,
- * n_cells * ppc <= 2^31 - 2^24.  The library allocates the device memory.  Initialisation
+ * body_force is F = F' H / v0^2 (Eq. 5); 1 <= n_cells <= 16384, ppc >= 1,
+ * n_cells * ppc <= 2^31 - 2^24 (with group_size 512 and more than ~12,000 cells the
+ * step's shared memory may not fit: DSMC_E_INVAL).  The library allocates the device memory.  Initialisation
  * is enqueued on the legacy default stream and completed before return. */
 DSMC_API dsmc_status dsmc_create(const dsmc_gas* gas, double Kn, double wall_T,
                         double body_force, int n_cells, int ppc, uint64_t seed,

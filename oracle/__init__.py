@@ -77,6 +77,8 @@ def lib() -> ctypes.CDLL:
             L.or_scatter_pair.argtypes = [fp, fp, c.c_uint64, c.c_uint32, c.c_uint32,
                                           c.c_uint32, c.c_uint32]
             L.or_scatter_pair.restype = c.c_int
+            L.or_accept_threshold.argtypes = [c.c_void_p, c.c_float, c.c_float]
+            L.or_accept_threshold.restype = c.c_float
             L.or_group_count.argtypes = [c.c_int, c.c_int]
             L.or_group_count.restype = c.c_int
             L.or_create.argtypes = [c.c_double, c.c_double, c.c_double, c.c_int, c.c_int,
@@ -235,11 +237,11 @@ class OracleSim:
         return lib().or_error(self.h)
 
     def params(self):
-        f = np.zeros(6, np.float32)
+        f = np.zeros(7, np.float32)
         d = np.zeros(2, np.float64)
         lib().or_params(self.h, _ptr(f), _ptr(d))
         return {"dt": f[0], "F": f[1], "coef": f[2], "cvhs": f[3], "vexp": f[4],
-                "smax0": f[5], "nsig": d[0], "dt_d": d[1]}
+                "smax0": f[5], "vinv": f[6], "nsig": d[0], "dt_d": d[1]}
 
     def state(self):
         arrs = [np.empty(self.N, np.float32) for _ in range(4)]
@@ -268,6 +270,9 @@ class OracleSim:
 
     def reset_samples(self):
         lib().or_reset_samples(self.h)
+
+    def accept_threshold(self, u: float, smax: float) -> float:
+        return lib().or_accept_threshold(self.h, float(u), float(smax))
 
 
 def fields(acc: np.ndarray, n_samples: int, ppc: int) -> dict:

@@ -47,8 +47,9 @@
  *   Gaussian / wall   pinned: moments and Kolmogorov-Smirnov against N(0,1/2) and the
  *                     flux-weighted half-Maxwellian.
  *   collision         pinned: momentum and energy conservation per collision,
- *                     isotropy of the post-collision direction, HS collision rate
- *                     N(N-1) sigma <g> dt / (2V) at equilibrium.
+ *                     isotropy of the post-collision direction, HS and VHS collision
+ *                     rate N(N-1) sigma <g> dt / (2V) at equilibrium, acceptance
+ *                     probability sigma g / (sigma g)_max against its definition.
  *   move + walls      pinned: collisionless transient closed form (1D quadrature).
  *   sort              pinned: brute-force stable sort by (cell, previous slot).
  *   whole step        pinned: Maxwellian preservation, momentum balance
@@ -279,14 +280,14 @@ typedef struct {
   /* derived */
   int N;
   double nsig, dt_d;
-  float dt, F, coef, cvhs, vexp, smax0, ncf;
+  float dt, F, coef, cvhs, vexp, vinv, smax0, ncf;
   /* state: sorted by cell */
   float *y, *vx, *vy, *vz;
   float *ty, *tvx, *tvy, *tvz; /* sort scratch */
   int* cell;                   /* per slot */
   int* offset;                 /* n_cells + 1 */
   float* smax;                 /* (sigma g)_max per cell, units sigma_ref v0 */
-  float* smax_obs;
+  float* gmax_obs;              /* largest candidate relative speed of the step */
   unsigned long long *ncand, *nacc;
   double* acc;  /* n_cells x 13 raw sums */
   double* aacc; /* n_cells x 13 sums of absolute values (error bounds of other
@@ -415,6 +416,21 @@ static float sigma_g(const osim* s, float g) {
   return s->cvhs * or_pow(g, s->vexp);
 }
 
+/* NTC acceptance, sigma(g) g > u (sigma g)_max (probability sigma g / (sigma g)_max),
+ * written as a threshold on the relative speed, g > thr:
+ *   hard spheres:  thr = u (sigma g)_max;
+ *   VHS, w < 1:    thr = (u (sigma g)_max / cvhs)^(1/(2-2w)), since sigma g grows
+ *                  monotonically with g;
+ *   w = 1:         sigma g = cvhs for every g: thr = -1 (accept) when
+ *                  u (sigma g)_max < cvhs, else +inf (reject). */
+static float accept_threshold(const osim* s, float u, float smax) {
+  float us = u * smax;
+  if (s->omega == 0.5) return us;
+  if (s->omega == 1.0) return (us < s->cvhs) ? -1.0f : INFINITY;
+  float t = us / s->cvhs;
+  return or_exp(s->vinv * or_ln(t));
+}
+
 /* Post-collision velocities of an accepted pair (isotropic scattering, which both
  * HS and VHS share): the relative speed g is kept, its direction is drawn uniformly
  * on the sphere by Marsaglia's (1972) method from the sphere sub-draws of the
@@ -456,6 +472,11 @@ OR_EXPORT int or_scatter_pair(float* vi, float* vj, uint64_t seed, uint32_t k,
   return scatter_pair(vi, vj, g, &f);
 }
 
+/* Exposed for the acceptance pin. */
+OR_EXPORT float or_accept_threshold(const osim* s, float u, float smax) {
+  return accept_threshold(s, u, smax);
+}
+
 /* Collision groups of a cell holding nc particles: consecutive runs of G sorted
  * particles, the last run taking the remainder, and a remainder below G/2 merged into
  * the run before it, so every group but a lone one has at least G/2 particles. */
@@ -470,7 +491,9 @@ OR_EXPORT int or_group_count(int nc, int G) {
  * ng of the nc particles of cell c, with the group volume ng/nc of the cell's):
  *   M = (ng - 1) nc (n sigma_ref) dt / (2 ppc) * (sigma g)_max,
  * rounded stochastically; each candidate picks i != j uniformly and is accepted with
- * probability sigma g / (sigma g)_max.  Candidates are applied in order. */
+ * probability sigma g / (sigma g)_max (accept_threshold).  Candidates are applied in
+ * order.  The largest relative speed among the candidates is kept for the update of
+ * (sigma g)_max after the step. */
 static void collide_group(osim* s, int c, int nc, int gic, int start, int ng) {
   if (ng < 2) return;
   float smax = s->smax[c];
@@ -502,9 +525,8 @@ static void collide_group(osim* s, int c, int nc, int gic, int start, int ng) {
     float gy = vy[i] - vy[j];
     float gz = vz[i] - vz[j];
     float g = sqrtf(gx * gx + gy * gy + gz * gz);
-    float sg = sigma_g(s, g);
-    if (sg > s->smax_obs[c]) s->smax_obs[c] = sg;
-    if (or_u01(w[2]) * smax < sg) {
+    if (g > s->gmax_obs[c]) s->gmax_obs[c] = g;
+    if (g > accept_threshold(s, or_u01(w[2]), smax)) {
       float vi[3] = {vx[i], vy[i], vz[i]};
       float vj[3] = {vx[j], vy[j], vz[j]};
       family f = {s->seed, k, (uint32_t)c, st, c3, 0};
@@ -520,7 +542,7 @@ static void collide_group(osim* s, int c, int nc, int gic, int start, int ng) {
 }
 
 static void collide_all(osim* s) {
-  for (int c = 0; c < s->n_cells; ++c) s->smax_obs[c] = 0.0f;
+  for (int c = 0; c < s->n_cells; ++c) s->gmax_obs[c] = 0.0f;
   for (int c = 0; c < s->n_cells; ++c) {
     int start = s->offset[c];
     int nc = s->offset[c + 1] - start;
@@ -531,9 +553,12 @@ static void collide_all(osim* s) {
       collide_group(s, c, nc, g, gs, gn);
     }
   }
-  /* (sigma g)_max is raised after the step, so it never depends on group order. */
-  for (int c = 0; c < s->n_cells; ++c)
-    if (s->smax_obs[c] > s->smax[c]) s->smax[c] = s->smax_obs[c];
+  /* (sigma g)_max is raised after the step to sigma g of the largest candidate
+   * relative speed, so it never depends on group order. */
+  for (int c = 0; c < s->n_cells; ++c) {
+    float sg = sigma_g(s, s->gmax_obs[c]);
+    if (sg > s->smax[c]) s->smax[c] = sg;
+  }
 }
 
 /* Raw moment sums per cell (Sec. 3: DSMC results are time averages): count,
@@ -583,7 +608,7 @@ OR_EXPORT void or_destroy(osim* s) {
   if (!s) return;
   free(s->y); free(s->vx); free(s->vy); free(s->vz);
   free(s->ty); free(s->tvx); free(s->tvy); free(s->tvz);
-  free(s->cell); free(s->offset); free(s->smax); free(s->smax_obs);
+  free(s->cell); free(s->offset); free(s->smax); free(s->gmax_obs);
   free(s->ncand); free(s->nacc); free(s->acc); free(s->aacc);
   free(s);
 }
@@ -620,6 +645,7 @@ OR_EXPORT osim* or_create(double omega, double Kn, double F, int n_cells, int pp
   double cv = (omega == 0.5) ? 1.0 : pow(2.0, omega - 0.5) / tgamma(2.5 - omega);
   s->cvhs = (float)cv;
   s->vexp = (float)(2.0 - 2.0 * omega);
+  s->vinv = (omega < 1.0) ? (float)(1.0 / (2.0 - 2.0 * omega)) : 0.0f;
   s->smax0 = (float)(cv * pow(5.0, 2.0 - 2.0 * omega));
   s->ncf = (float)n_cells;
   size_t n = (size_t)s->N, nb = n ? n : 1;
@@ -628,7 +654,7 @@ OR_EXPORT osim* or_create(double omega, double Kn, double F, int n_cells, int pp
   s->cell = malloc(nb * sizeof(int));
   s->offset = calloc((size_t)n_cells + 1, sizeof(int));
   s->smax = malloc((size_t)n_cells * 4);
-  s->smax_obs = malloc((size_t)n_cells * 4);
+  s->gmax_obs = malloc((size_t)n_cells * 4);
   s->ncand = calloc((size_t)n_cells, sizeof(unsigned long long));
   s->nacc = calloc((size_t)n_cells, sizeof(unsigned long long));
   s->acc = calloc((size_t)n_cells * NMOM, sizeof(double));
@@ -663,11 +689,11 @@ OR_EXPORT int or_n_particles(const osim* s) { return s->N; }
 OR_EXPORT long long or_step_count(const osim* s) { return s->step; }
 OR_EXPORT int or_error(const osim* s) { return s->err; }
 
-/* dt, F, coef, cvhs, vexp, smax0 as the binary32 values the step uses, and nsig,
- * dt in binary64. */
+/* dt, F, coef, cvhs, vexp, smax0, vinv as the binary32 values the step uses, and
+ * nsig, dt in binary64. */
 OR_EXPORT void or_params(const osim* s, float* f6, double* d2) {
   f6[0] = s->dt; f6[1] = s->F; f6[2] = s->coef; f6[3] = s->cvhs; f6[4] = s->vexp;
-  f6[5] = s->smax0;
+  f6[5] = s->smax0; f6[6] = s->vinv;
   d2[0] = s->nsig; d2[1] = s->dt_d;
 }
 

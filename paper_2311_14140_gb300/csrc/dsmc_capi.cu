@@ -34,17 +34,44 @@ dsmc_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-enum KernelId { K_INIT = 0, K_COLLIDE, K_MOVE_COUNT, K_SCAN, K_OFFSETS, K_SCATTER, K_NUM };
-const char* const kKernelNames[K_NUM] = {"init",         "collide_sample", "move_count",
-                                         "scan_hist",    "cell_offsets",   "scatter"};
+enum KernelId {
+  K_INIT = 0,
+  K_COLLIDE_MOVE,
+  K_SCAN,
+  K_OFFSETS,
+  K_SCATTER_SPANS,
+  K_INDEX_COUNT,
+  K_INDEX_SCATTER,
+  K_NUM
+};
+const char* const kKernelNames[K_NUM] = {"init",          "collide_move", "scan_hist",
+                                         "cell_offsets",  "scatter_spans", "index_count",
+                                         "index_scatter"};
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Layout {
   int n_cap;
-  SortPlan plan;
+  SortPlan plan;  // fixed spans of slots for the stand-alone sort into cells
+  int cps;        // cells per span of the step passes
+  int n_spans;
   size_t st, hist, count, offset, smax, ncand, nacc, acc, err, total;
 };
+
+// Spans of the step: consecutive cells, enough of them that a span holds a few
+// thousand particles at the initial density and that there are at most kMaxSpans.
+void make_spans(int n_cells, int ppc, int* cps, int* n_spans) {
+  const long long N = (long long)n_cells * ppc;
+  long long target = (N + kMaxSpans - 1) / kMaxSpans;
+  if (target < 2048) target = 2048;
+  long long c = (target + ppc - 1) / ppc;
+  if (c < (n_cells + kMaxSpans - 1) / kMaxSpans) c = (n_cells + kMaxSpans - 1) / kMaxSpans;
+  if (c > kMaxCellsPerSpan) c = kMaxCellsPerSpan;
+  if (c > n_cells) c = n_cells;
+  if (c < 1) c = 1;
+  *cps = (int)c;
+  *n_spans = (int)((n_cells + c - 1) / c);
+}
 
 SortPlan make_plan(long long N, int n_cells) {
   long long w = (N + 255) / 256;
@@ -62,19 +89,22 @@ SortPlan make_plan(long long N, int n_cells) {
   return SortPlan{(int)w, (int)span, (int)wpb};
 }
 
-Layout make_layout(int n_cells, long long N) {
+Layout make_layout(int n_cells, int ppc) {
   Layout L{};
+  const long long N = (long long)n_cells * ppc;
   L.n_cap = (int)((N + 63) & ~63LL);
   L.plan = make_plan(N, n_cells);
+  make_spans(n_cells, ppc, &L.cps, &L.n_spans);
+  const size_t rows = (size_t)(L.plan.n_warps > L.n_spans ? L.plan.n_warps : L.n_spans);
   size_t o = 0;
   L.st = o;
   o += align256(8 * (size_t)L.n_cap * sizeof(float));
   L.hist = o;
-  o += align256((size_t)L.plan.n_warps * n_cells * sizeof(int));
+  o += align256(rows * n_cells * sizeof(int));
   L.count = o;
   o += align256((size_t)n_cells * sizeof(int));
-  L.offset = o;
-  o += align256(((size_t)n_cells + 1) * sizeof(int));
+  L.offset = o;  // two arrays of n_cells + 1: current and next
+  o += align256(2 * ((size_t)n_cells + 1) * sizeof(int));
   L.smax = o;
   o += align256(2 * (size_t)n_cells * sizeof(float));
   L.ncand = o;
@@ -93,7 +123,7 @@ Layout make_layout(int n_cells, long long N) {
 // use them.
 struct Params {
   double nsig, dt;
-  float dt_f, F_f, coef, cvhs, vexp, smax0;
+  float dt_f, F_f, coef, cvhs, vexp, vinv, smax0;
 };
 
 // n sigma_ref H from Kn through mu0 v0 / (P0 H) = 2 Kn / sqrt(pi) (Eq. 7) and the
@@ -128,6 +158,7 @@ bool derive_params(double omega, double Kn, double F, int ppc, const dsmc_option
   p->coef = (float)(nsig * dt / (2.0 * (double)ppc));
   p->cvhs = (float)cv;
   p->vexp = (float)(2.0 - 2.0 * omega);
+  p->vinv = (omega < 1.0) ? (float)(1.0 / (2.0 - 2.0 * omega)) : 0.0f;
   p->smax0 = (float)(cv * std::pow(5.0, 2.0 - 2.0 * omega));
   return std::isfinite(dt) && dt > 0.0;
 }
@@ -173,7 +204,9 @@ struct dsmc_sim {
   bool owns = false;
   DevState st[2]{};
   int cur = 0;
-  int *hist = nullptr, *count = nullptr, *offset = nullptr, *err = nullptr;
+  int *hist = nullptr, *count = nullptr, *err = nullptr;
+  int* off[2]{};
+  int ocur = 0;
   float* smax[2]{};
   int scur = 0;
   unsigned long long *ncand = nullptr, *nacc = nullptr;
@@ -233,30 +266,74 @@ dsmc_status collect_times(dsmc_sim* h) {
   return DSMC_OK;
 }
 
-// Move (when do_move) and sort into cells: histogram, prefix over partitions and
-// cells, stable scatter into the other buffer.
-dsmc_status run_index(dsmc_sim* h, bool do_move) {
-  const MoveArgs m{h->p.dt_f, h->p.F_f, h->k0(), h->k1(), (uint32_t)h->step, do_move ? 1 : 0};
+// Sort into cells without moving (creation, state load): histogram over fixed spans
+// of slots, prefix over spans and cells, stable scatter into the other buffer.
+dsmc_status run_index(dsmc_sim* h) {
+  const MoveArgs m{0.0f, 0.0f, h->k0(), h->k1(), (uint32_t)h->step, 0};
   const int N = (int)h->N;
   cudaStream_t s = h->stream();
-  DSMC_CUDA(timed(h, K_MOVE_COUNT, [&] {
+  int* off_new = h->off[h->ocur ^ 1];
+  DSMC_CUDA(timed(h, K_INDEX_COUNT, [&] {
               return launch_move_count(h->st[h->cur], N, h->L.plan, h->n_cells, h->ncf, m,
                                        h->hist, h->err, s);
             }),
-            "move_count");
+            "index_count");
   DSMC_CUDA(timed(h, K_SCAN,
                   [&] { return launch_scan_hist(h->hist, h->L.plan.n_warps, h->n_cells, h->count, s); }),
             "scan_hist");
   DSMC_CUDA(timed(h, K_OFFSETS,
-                  [&] { return launch_cell_offsets(h->count, h->n_cells, h->offset, s); }),
+                  [&] { return launch_cell_offsets(h->count, h->n_cells, off_new, s); }),
             "cell_offsets");
-  DSMC_CUDA(timed(h, K_SCATTER, [&] {
+  DSMC_CUDA(timed(h, K_INDEX_SCATTER, [&] {
               return launch_scatter(h->st[h->cur], h->st[h->cur ^ 1], N, h->L.plan, h->n_cells,
-                                    h->ncf, h->hist, h->offset, h->err, s);
+                                    h->ncf, h->hist, off_new, h->err, s);
             }),
-            "scatter");
+            "index_scatter");
   h->cur ^= 1;
+  h->ocur ^= 1;
   return DSMC_OK;
+}
+
+// One step: collide + sample + move + count (one pass over the state, in place),
+// prefix over spans and cells, stable scatter into the other buffer.
+dsmc_status run_step(dsmc_sim* h) {
+  cudaStream_t s = h->stream();
+  const int G = h->opt.group_size;
+  const bool sampling = h->step >= h->opt.sample_start;
+  const bool collide = h->opt.collisions != 0 && h->p.nsig > 0.0;
+  const int mode = (h->omega == 0.5) ? 0 : (h->omega == 1.0 ? 2 : 1);
+  const StepArgs a{h->n_cells, h->L.cps, G + G / 2 - 1, G, h->ncf, h->p.dt_f, h->p.F_f,
+                   h->p.coef, h->p.cvhs, h->p.vexp, h->p.vinv, h->k0(), h->k1(),
+                   (uint32_t)h->step, sampling ? 1 : 0, collide ? 1 : 0, mode};
+  int* off_cur = h->off[h->ocur];
+  int* off_new = h->off[h->ocur ^ 1];
+  DSMC_CUDA(timed(h, K_COLLIDE_MOVE, [&] {
+              return launch_collide_move(h->st[h->cur], off_cur, h->smax[h->scur],
+                                         h->smax[h->scur ^ 1], h->ncand, h->nacc, h->acc,
+                                         h->hist, a, h->L.n_spans, h->err, s);
+            }),
+            "collide_move");
+  h->scur ^= 1;
+  DSMC_CUDA(timed(h, K_SCAN,
+                  [&] { return launch_scan_hist(h->hist, h->L.n_spans, h->n_cells, h->count, s); }),
+            "scan_hist");
+  DSMC_CUDA(timed(h, K_OFFSETS,
+                  [&] { return launch_cell_offsets(h->count, h->n_cells, off_new, s); }),
+            "cell_offsets");
+  DSMC_CUDA(timed(h, K_SCATTER_SPANS, [&] {
+              return launch_scatter_spans(h->st[h->cur], h->st[h->cur ^ 1], off_cur, off_new,
+                                          h->hist, h->n_cells, h->L.cps, h->L.n_spans, h->ncf,
+                                          (int)h->N, h->err, s);
+            }),
+            "scatter_spans");
+  h->cur ^= 1;
+  h->ocur ^= 1;
+  return DSMC_OK;
+}
+
+// The collide/move pass must fit one CTA's shared memory for this group size.
+bool step_fits(int n_cells, int cps, int G) {
+  return step_smem_layout(n_cells, cps, G + G / 2 - 1).total <= kStepSmemMax;
 }
 
 dsmc_status read_error_word(dsmc_sim* h) {
@@ -300,7 +377,7 @@ dsmc_status dsmc_default_options(dsmc_options* opt) {
 
 size_t dsmc_workspace_bytes(int n_cells, int ppc) {
   if (n_cells < 1 || ppc < 1) return 0;
-  return make_layout(n_cells, (long long)n_cells * ppc).total;
+  return make_layout(n_cells, ppc).total;
 }
 
 dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double body_force,
@@ -319,8 +396,7 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
   if (n_cells < 1 || ppc < 1) return fail(DSMC_E_INVAL, "n_cells and ppc must be >= 1");
   const long long N = (long long)n_cells * ppc;
   if (N > kMaxParticles) return fail(DSMC_E_INVAL, "n_cells * ppc must be <= 2^31 - 2^24");
-  if ((size_t)n_cells * sizeof(int) > kSortSmemMax)
-    return fail(DSMC_E_INVAL, "n_cells must be <= 51200");
+  if (n_cells > kMaxStepCells) return fail(DSMC_E_INVAL, "n_cells must be <= 16384");
   dsmc_options opt;
   dsmc_default_options(&opt);
   if (opt_in) opt = *opt_in;
@@ -329,6 +405,12 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
   Params p;
   if (!derive_params(gas->omega, Kn, body_force, ppc, opt, &p))
     return fail(DSMC_E_INVAL, "time step undefined: set options.dt for infinite Kn");
+  {
+    int cps, n_spans;
+    make_spans(n_cells, ppc, &cps, &n_spans);
+    if (!step_fits(n_cells, cps, opt.group_size))
+      return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
+  }
 
   dsmc_sim* h = new (std::nothrow) dsmc_sim();
   if (!h) return fail(DSMC_E_NOMEM, "host allocation failed");
@@ -347,7 +429,7 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
   h->ncf = (float)n_cells;
   h->seed = seed;
   h->opt = opt;
-  h->L = make_layout(n_cells, N);
+  h->L = make_layout(n_cells, ppc);
   if (workspace) {
     if (workspace_bytes < h->L.total || ((uintptr_t)workspace & 255u)) {
       delete h;
@@ -372,7 +454,8 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
                         f + (4 * k + 3) * nc};
   h->hist = (int*)(b + h->L.hist);
   h->count = (int*)(b + h->L.count);
-  h->offset = (int*)(b + h->L.offset);
+  h->off[0] = (int*)(b + h->L.offset);
+  h->off[1] = h->off[0] + (n_cells + 1);
   h->smax[0] = (float*)(b + h->L.smax);
   h->smax[1] = h->smax[0] + n_cells;
   h->ncand = (unsigned long long*)(b + h->L.ncand);
@@ -385,7 +468,8 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
     return s;
   };
   cudaStream_t s = h->stream();
-  ce = set_kernel_smem_limits(kSortSmemMax, collide_smem_bytes(kMaxGroup + kMaxGroup / 2 - 1));
+  ce = set_kernel_smem_limits(kSortSmemMax);
+  if (ce == cudaSuccess) ce = set_step_smem_limits(kStepSmemMax, kStepSmemMax);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaFuncSetAttribute"));
   if ((ce = cudaMemsetAsync(h->acc, 0, (size_t)n_cells * kNMom * sizeof(double), s)) != cudaSuccess ||
       (ce = cudaMemsetAsync(h->ncand, 0, (size_t)n_cells * 8, s)) != cudaSuccess ||
@@ -399,7 +483,7 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
   ce = timed(h, K_INIT,
              [&] { return launch_init(h->st[0], (int)N, ppc, h->ncf, h->k0(), h->k1(), h->err, s); });
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "init"));
-  st = run_index(h, false);
+  st = run_index(h);
   if (st != DSMC_OK) return bail(st);
   ce = cudaStreamSynchronize(s);  // smax0 host buffer must outlive the copy
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "stream sync"));
@@ -425,6 +509,8 @@ dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt) {
   Params p;
   if (!derive_params(h->omega, h->Kn, h->F, h->ppc, *opt, &p))
     return fail(DSMC_E_INVAL, "time step undefined: set options.dt for infinite Kn");
+  if (!step_fits(h->n_cells, h->L.cps, opt->group_size))
+    return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   if (h->events_used) {
     s = collect_times(h);
     if (s != DSMC_OK) return s;
@@ -440,26 +526,10 @@ dsmc_status dsmc_step(dsmc_handle h, int n_steps) {
   if (n_steps < 0) return fail(DSMC_E_INVAL, "n_steps must be >= 0");
   if (h->latched != DSMC_OK) return fail(h->latched, "an earlier step reached a device limit");
   DeviceGuard guard(h->device);
-  cudaStream_t st = h->stream();
-  const bool vhs = h->omega != 0.5;
-  const int G = h->opt.group_size;
   for (int it = 0; it < n_steps; ++it) {
     h->step += 1;
-    const bool sampling = h->step >= h->opt.sample_start;
-    const bool collide = h->opt.collisions != 0 && h->p.nsig > 0.0;
-    if (sampling || collide) {
-      const CollideArgs a{G, G + G / 2 - 1, h->p.coef, h->p.cvhs, h->p.vexp, h->k0(), h->k1(),
-                          (uint32_t)h->step, sampling ? 1 : 0, collide ? 1 : 0};
-      DSMC_CUDA(timed(h, K_COLLIDE, [&] {
-                  return launch_collide_sample(h->st[h->cur], h->n_cells, h->offset,
-                                               h->smax[h->scur], h->smax[h->scur ^ 1], h->ncand,
-                                               h->nacc, h->acc, a, vhs, h->err, st);
-                }),
-                "collide_sample");
-      h->scur ^= 1;
-    }
-    if (sampling) h->n_samples += 1;
-    s = run_index(h, true);
+    if (h->step >= h->opt.sample_start) h->n_samples += 1;
+    s = run_step(h);
     if (s != DSMC_OK) return s;
   }
   if (h->opt.profile) return collect_times(h);
@@ -520,7 +590,9 @@ dsmc_status dsmc_copy_cells(dsmc_handle h, int* offset, float* smax, unsigned lo
   cudaStream_t st = h->stream();
   const size_t nc = (size_t)h->n_cells;
   if (offset)
-    DSMC_CUDA(cudaMemcpyAsync(offset, h->offset, (nc + 1) * sizeof(int), cudaMemcpyDefault, st), "copy cells");
+    DSMC_CUDA(cudaMemcpyAsync(offset, h->off[h->ocur], (nc + 1) * sizeof(int), cudaMemcpyDefault,
+                              st),
+              "copy cells");
   if (smax)
     DSMC_CUDA(cudaMemcpyAsync(smax, h->smax[h->scur], nc * sizeof(float), cudaMemcpyDefault, st), "copy cells");
   if (ncand) DSMC_CUDA(cudaMemcpyAsync(ncand, h->ncand, nc * 8, cudaMemcpyDefault, st), "copy cells");
@@ -548,7 +620,7 @@ dsmc_status dsmc_load_state(dsmc_handle h, const float* y, const float* vx, cons
               "load smax");
   DSMC_CUDA(launch_clamp_y(d.y, (int)h->N, st), "clamp");
   h->step = step;
-  s = run_index(h, false);
+  s = run_index(h);
   if (s != DSMC_OK) return s;
   return dsmc_sync(h);
 }
@@ -572,10 +644,13 @@ dsmc_status dsmc_get_info(dsmc_handle h, dsmc_info* info) {
   info->coef = h->p.coef;
   info->cvhs = h->p.cvhs;
   info->vexp = h->p.vexp;
+  info->vinv = h->p.vinv;
   info->smax0 = h->p.smax0;
   info->device_bytes = h->L.total;
   info->sort_warps = h->L.plan.n_warps;
   info->sort_span = h->L.plan.span;
+  info->cells_per_span = h->L.cps;
+  info->n_spans = h->L.n_spans;
   return DSMC_OK;
 }
 

@@ -144,4 +144,53 @@ __device__ __forceinline__ int group_count(int nc, int G) {
   return ng;
 }
 
+// Free flight of one particle over dt with the body force along x and fully
+// diffuse walls at the wall temperature.  Returns false at the bounce limit.
+__device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, float dt,
+                                    float F, uint32_t k0, uint32_t k1, uint32_t step,
+                                    uint32_t slot) {
+  float t = dt;
+  bool ok = true;
+  for (int b = 0;; ++b) {
+    const float ynew = fadd(y, fmul(vy, t));
+    float thit, wall;
+    if (ynew < 0.0f) {
+      thit = fdiv(y, -vy);
+      wall = 0.0f;
+    } else if (ynew > 1.0f) {
+      thit = fdiv(fsub(1.0f, y), vy);
+      wall = 1.0f;
+    } else {
+      y = ynew;
+      vx = fadd(vx, fmul(F, t));
+      return ok;
+    }
+    if (b >= kMaxBounces) {  // leave the particle on the wall
+      y = wall;
+      return false;
+    }
+    if (thit > t) thit = t;
+    t = fsub(t, thit);
+    const uint32_t c1 = (uint32_t)b << 8;
+    const uint32_t c3 = kStreamMove << 24;
+    U4 w = philox(slot, c1, step, c3, k0, k1);
+    const float speed = fsqrt(-ln32(u01(w.x)));
+    float z0 = 0.0f, z1 = 0.0f;
+    bool got = false;
+    for (int a = 0; a < kNormalAttempts && !got; ++a) {
+      if ((a & 1) == 0) w = philox(slot, c1 | (1u + (uint32_t)(a >> 1)), step, c3, k0, k1);
+      got = (a & 1) ? polar_pair(w.z, w.w, z0, z1) : polar_pair(w.x, w.y, z0, z1);
+    }
+    if (!got) {
+      z0 = 0.0f;
+      z1 = 0.0f;
+      ok = false;
+    }
+    vx = z0;
+    vz = z1;
+    vy = (wall == 0.0f) ? speed : -speed;
+    y = wall;
+  }
+}
+
 }  // namespace dsmc

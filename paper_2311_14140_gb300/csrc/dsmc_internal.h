@@ -9,8 +9,13 @@
 namespace dsmc {
 
 constexpr int kNMom = 13;          // raw moment sums per cell
-constexpr int kCollideWarps = 4;   // warps (concurrent groups) per collision CTA
 constexpr int kMaxGroup = 512;     // largest collision group size G
+constexpr int kAWarps = 8;         // warps per CTA of the collide/move pass
+constexpr int kBWarpsMax = 4;      // warps (spans) per CTA of the span scatter
+constexpr int kMaxStepCells = 16384;
+constexpr int kMaxSpans = 152 * 16;   // rows of the per-step sort matrix, at most
+constexpr int kMaxCellsPerSpan = 256;
+constexpr size_t kStepSmemMax = 220 * 1024;
 constexpr int kSortWarpsMax = 152 * 16;
 constexpr int kSortWarpsPerBlock = 8;
 constexpr size_t kSortSmemMax = 200 * 1024;
@@ -51,17 +56,50 @@ struct MoveArgs {
   int do_move;
 };
 
-struct CollideArgs {
+// Arguments of the collide/move pass.
+struct StepArgs {
+  int n_cells;
+  int cps;   // cells per span (one CTA each)
+  int cap;   // largest group: G + G/2 - 1
   int G;
-  int cap;  // largest group: G + G/2 - 1
-  float coef;
-  float cvhs;
-  float vexp;
-  uint32_t k0, k1;
+  float ncf;
+  float dt, F;
+  float coef;              // n sigma_ref dt / (2 ppc)
+  float cvhs, vexp, vinv;  // VHS factor, exponent 2 - 2 omega and its inverse
+  uint32_t k0, k1;         // Philox key (seed)
   uint32_t step;
   int sample;
   int collide;
+  int mode;  // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
 };
+
+// Dynamic shared memory of one collide/move CTA (byte offsets).
+struct StepSmem {
+  size_t hist, cell_acc, cell_cand, cell_accn, cell_gmax, warps, per_warp, total;
+};
+
+__host__ __device__ inline size_t step_align(size_t o, size_t a) { return (o + a - 1) / a * a; }
+
+__host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int cap) {
+  StepSmem L;
+  size_t o = 0;
+  L.hist = o;
+  o = step_align(o + (size_t)n_cells * 4, 8);
+  L.cell_acc = o;
+  o += (size_t)cps * kNMom * 8;
+  L.cell_cand = o;
+  o += (size_t)cps * 8;
+  L.cell_accn = o;
+  o += (size_t)cps * 8;
+  L.cell_gmax = o;
+  o = step_align(o + (size_t)cps * 4, 16);
+  // per warp: vx, vy, vz, owner (cap words each) and 13 x 32 lane accumulators
+  L.per_warp = step_align((size_t)cap * 16 + (size_t)kNMom * 32 * 4, 16);
+  L.warps = o;
+  o += (size_t)kAWarps * L.per_warp;
+  L.total = o;
+  return L;
+}
 
 cudaError_t launch_init(const DevState& s, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
                         int* err, cudaStream_t st);
@@ -73,14 +111,18 @@ cudaError_t launch_cell_offsets(const int* count, int n_cells, int* offset, cuda
 cudaError_t launch_scatter(const DevState& from, const DevState& to, int N, const SortPlan& sp,
                            int n_cells, float ncf, const int* hist, const int* offset,
                            int* err, cudaStream_t st);
-size_t collide_smem_bytes(int cap);
-cudaError_t launch_collide_sample(const DevState& s, int n_cells, const int* offset,
-                                  const float* smax_in, float* smax_out,
-                                  unsigned long long* ncand, unsigned long long* nacc,
-                                  double* acc, const CollideArgs& a, bool vhs, int* err,
-                                  cudaStream_t st);
 cudaError_t launch_clamp_y(float* y, int N, cudaStream_t st);
-cudaError_t set_kernel_smem_limits(size_t sort_bytes, size_t collide_bytes);
+cudaError_t set_kernel_smem_limits(size_t sort_bytes);
+
+cudaError_t launch_collide_move(const DevState& s, const int* off, const float* smax_in,
+                                float* smax_out, unsigned long long* ncand,
+                                unsigned long long* nacc, double* acc, int* hist,
+                                const StepArgs& a, int n_spans, int* err, cudaStream_t st);
+int scatter_spans_warps(int n_cells);
+cudaError_t launch_scatter_spans(const DevState& from, const DevState& to, const int* off_cur,
+                                 const int* off_new, const int* hist, int n_cells, int cps,
+                                 int n_spans, float ncf, int N, int* err, cudaStream_t st);
+cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes);
 
 // Sets the message dsmc_last_error() returns on the calling thread.
 void set_last_error(const std::string& msg);

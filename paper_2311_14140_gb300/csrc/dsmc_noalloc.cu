@@ -107,8 +107,7 @@ extern "C" dsmc_status dsmc_sort_cells_static(const float* y, const float* vx, c
   // The error word must start at zero; the histogram and totals are fully rewritten.
   e = cudaMemsetAsync(err, 0, sizeof(int), st);
   if (e == cudaSuccess)
-    e = set_kernel_smem_limits(kSortSmemMax,
-                               collide_smem_bytes(kMaxGroup + kMaxGroup / 2 - 1));
+    e = set_kernel_smem_limits(kSortSmemMax);
   const MoveArgs no_move{0.0f, 0.0f, 0u, 0u, 0u, 0};
   const DevState in{const_cast<float*>(y), const_cast<float*>(vx), const_cast<float*>(vy),
                     const_cast<float*>(vz)};

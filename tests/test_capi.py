@@ -44,7 +44,7 @@ def test_default_options(lib):
     o = D.default_options()
     assert (o.dt_factor, o.dt, o.sample_start, o.group_size, o.collisions, o.profile) == \
         (0.2, 0.0, 0, 256, 1, 0)
-    assert lib.dsmc_kernel_count() == 6
+    assert lib.dsmc_kernel_count() == 7
     assert lib.dsmc_kernel_name(0) == b"init"
     assert lib.dsmc_status_string(4) == b"device limit reached"
 
@@ -70,7 +70,7 @@ def _create(lib, gas=None, Kn=1.0, wall_T=273.0, F=0.0, n_cells=10, ppc=10, opt=
     (dict(Kn=0.0), "Kn"), (dict(Kn=-1.0), "Kn"), (dict(Kn=math.nan), "Kn"),
     (dict(wall_T=0.0), "wall_T"), (dict(F=math.inf), "body_force"),
     (dict(n_cells=0), "n_cells"), (dict(ppc=0), "ppc"),
-    (dict(n_cells=70000, ppc=1), "51200"), (dict(n_cells=50000, ppc=50000), "2^31 - 2^24"),
+    (dict(n_cells=70000, ppc=1), "16384"), (dict(n_cells=50000, ppc=50000), "2^31 - 2^24"),
     (dict(Kn=math.inf), "time step"),
 ])
 def test_bad_arguments_are_rejected(lib, kw, needle):

@@ -151,3 +151,21 @@ def test_collision_direction_is_isotropic():
     from scipy import stats
     for c in range(3):
         assert stats.kstest(n[:, c], lambda x: (np.asarray(x) + 1) / 2).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("omega", [0.5, 0.74, 0.81, 1.0])
+def test_acceptance_probability_is_sigma_g_over_max(omega):
+    """NTC accepts a candidate of relative speed g with probability
+    sigma(g) g / (sigma g)_max (sigma(g) g = cvhs g^(2 - 2 omega) in sigma_ref v0 units):
+    the fraction of a fine uniform grid of u accepted through the threshold g > thr(u)
+    matches it."""
+    s = oracle.OracleSim(omega=omega, Kn=1.0, n_cells=1, ppc=2)
+    p = s.params()
+    cv, a = float(p["cvhs"]), float(p["vexp"])
+    smax = float(p["smax0"])
+    words = (np.arange(4096, dtype=np.uint64) * 2 ** 20 + 2 ** 19).astype(np.uint32)
+    us = [oracle.u01(int(x)) for x in words]
+    thr = np.array([s.accept_threshold(u, smax) for u in us])
+    for g in (0.05, 0.4, 1.0, 1.7, 3.0, 4.9):
+        frac = float((g > thr).mean())
+        assert abs(frac - min(1.0, cv * g ** a / smax)) < 2.0 / len(us), (g, frac)
