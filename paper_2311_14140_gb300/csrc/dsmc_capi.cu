@@ -202,7 +202,7 @@ struct dsmc_sim {
   Layout L{};
   void* ws = nullptr;
   bool owns = false;
-  DevState st[2]{};
+  float4* P[2]{};  // particle records (y, vx, vy, vz), double-buffered for the sort
   int cur = 0;
   int *hist = nullptr, *count = nullptr, *err = nullptr;
   int* off[2]{};
@@ -266,27 +266,41 @@ dsmc_status collect_times(dsmc_sim* h) {
   return DSMC_OK;
 }
 
-// Sort into cells without moving (creation, state load): histogram over fixed spans
-// of slots, prefix over spans and cells, stable scatter into the other buffer.
+StepArgs step_args(const dsmc_sim* h, bool count_only) {
+  const int G = h->opt.group_size;
+  const bool sampling = h->step >= h->opt.sample_start;
+  const bool collide = h->opt.collisions != 0 && h->p.nsig > 0.0;
+  const int mode = (h->omega == 0.5) ? 0 : (h->omega == 1.0 ? 2 : 1);
+  return StepArgs{h->n_cells, h->L.cps, G + G / 2 - 1, G, h->ncf, h->p.dt_f, h->p.F_f,
+                  h->p.coef, h->p.cvhs, h->p.vexp, h->p.vinv, h->k0(), h->k1(),
+                  (uint32_t)h->step, (sampling && !count_only) ? 1 : 0,
+                  (collide && !count_only) ? 1 : 0, mode, count_only ? 1 : 0};
+}
+
+// Sort into cells without moving (creation, state load).  off[ocur] must describe
+// spans of slots (slot ranges per cell span); the records may be in any order within
+// them.  Counting pass over the spans, prefix over spans and cells, stable scatter.
 dsmc_status run_index(dsmc_sim* h) {
-  const MoveArgs m{0.0f, 0.0f, h->k0(), h->k1(), (uint32_t)h->step, 0};
-  const int N = (int)h->N;
   cudaStream_t s = h->stream();
+  const StepArgs a = step_args(h, /*count_only=*/true);
+  int* off_cur = h->off[h->ocur];
   int* off_new = h->off[h->ocur ^ 1];
   DSMC_CUDA(timed(h, K_INDEX_COUNT, [&] {
-              return launch_move_count(h->st[h->cur], N, h->L.plan, h->n_cells, h->ncf, m,
-                                       h->hist, h->err, s);
+              return launch_collide_move(h->P[h->cur], off_cur, h->smax[h->scur],
+                                         h->smax[h->scur ^ 1], h->ncand, h->nacc, h->acc,
+                                         h->hist, a, h->L.n_spans, h->err, s);
             }),
             "index_count");
   DSMC_CUDA(timed(h, K_SCAN,
-                  [&] { return launch_scan_hist(h->hist, h->L.plan.n_warps, h->n_cells, h->count, s); }),
+                  [&] { return launch_scan_hist(h->hist, h->L.n_spans, h->n_cells, h->count, s); }),
             "scan_hist");
   DSMC_CUDA(timed(h, K_OFFSETS,
                   [&] { return launch_cell_offsets(h->count, h->n_cells, off_new, s); }),
             "cell_offsets");
   DSMC_CUDA(timed(h, K_INDEX_SCATTER, [&] {
-              return launch_scatter(h->st[h->cur], h->st[h->cur ^ 1], N, h->L.plan, h->n_cells,
-                                    h->ncf, h->hist, off_new, h->err, s);
+              return launch_scatter_spans(h->P[h->cur], h->P[h->cur ^ 1], off_cur, off_new,
+                                          h->hist, h->n_cells, h->L.cps, h->L.n_spans, h->ncf,
+                                          (int)h->N, h->err, s);
             }),
             "index_scatter");
   h->cur ^= 1;
@@ -294,21 +308,26 @@ dsmc_status run_index(dsmc_sim* h) {
   return DSMC_OK;
 }
 
-// One step: collide + sample + move + count (one pass over the state, in place),
+// Spans of slots for a sort of records in arbitrary order: cell span k covers slots
+// [off[k cps], off[(k+1) cps]) with off[c] = floor(c N / n_cells).
+dsmc_status set_uniform_offsets(dsmc_sim* h, std::vector<int>& host) {
+  host.resize((size_t)h->n_cells + 1);
+  for (int c = 0; c <= h->n_cells; ++c) host[c] = (int)((long long)c * h->N / h->n_cells);
+  DSMC_CUDA(cudaMemcpyAsync(h->off[h->ocur], host.data(), host.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, h->stream()),
+            "offsets");
+  return DSMC_OK;
+}
+
+// One step: collide + sample + move + count (one pass over the records, in place),
 // prefix over spans and cells, stable scatter into the other buffer.
 dsmc_status run_step(dsmc_sim* h) {
   cudaStream_t s = h->stream();
-  const int G = h->opt.group_size;
-  const bool sampling = h->step >= h->opt.sample_start;
-  const bool collide = h->opt.collisions != 0 && h->p.nsig > 0.0;
-  const int mode = (h->omega == 0.5) ? 0 : (h->omega == 1.0 ? 2 : 1);
-  const StepArgs a{h->n_cells, h->L.cps, G + G / 2 - 1, G, h->ncf, h->p.dt_f, h->p.F_f,
-                   h->p.coef, h->p.cvhs, h->p.vexp, h->p.vinv, h->k0(), h->k1(),
-                   (uint32_t)h->step, sampling ? 1 : 0, collide ? 1 : 0, mode};
+  const StepArgs a = step_args(h, /*count_only=*/false);
   int* off_cur = h->off[h->ocur];
   int* off_new = h->off[h->ocur ^ 1];
   DSMC_CUDA(timed(h, K_COLLIDE_MOVE, [&] {
-              return launch_collide_move(h->st[h->cur], off_cur, h->smax[h->scur],
+              return launch_collide_move(h->P[h->cur], off_cur, h->smax[h->scur],
                                          h->smax[h->scur ^ 1], h->ncand, h->nacc, h->acc,
                                          h->hist, a, h->L.n_spans, h->err, s);
             }),
@@ -321,7 +340,7 @@ dsmc_status run_step(dsmc_sim* h) {
                   [&] { return launch_cell_offsets(h->count, h->n_cells, off_new, s); }),
             "cell_offsets");
   DSMC_CUDA(timed(h, K_SCATTER_SPANS, [&] {
-              return launch_scatter_spans(h->st[h->cur], h->st[h->cur ^ 1], off_cur, off_new,
+              return launch_scatter_spans(h->P[h->cur], h->P[h->cur ^ 1], off_cur, off_new,
                                           h->hist, h->n_cells, h->L.cps, h->L.n_spans, h->ncf,
                                           (int)h->N, h->err, s);
             }),
@@ -447,11 +466,8 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
     h->owns = true;
   }
   char* b = (char*)h->ws;
-  float* f = (float*)(b + h->L.st);
-  const size_t nc = (size_t)h->L.n_cap;
-  for (int k = 0; k < 2; ++k)
-    h->st[k] = DevState{f + (4 * k + 0) * nc, f + (4 * k + 1) * nc, f + (4 * k + 2) * nc,
-                        f + (4 * k + 3) * nc};
+  h->P[0] = (float4*)(b + h->L.st);
+  h->P[1] = h->P[0] + h->L.n_cap;
   h->hist = (int*)(b + h->L.hist);
   h->count = (int*)(b + h->L.count);
   h->off[0] = (int*)(b + h->L.offset);
@@ -468,8 +484,7 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
     return s;
   };
   cudaStream_t s = h->stream();
-  ce = set_kernel_smem_limits(kSortSmemMax);
-  if (ce == cudaSuccess) ce = set_step_smem_limits(kStepSmemMax, kStepSmemMax);
+  ce = set_step_smem_limits(kStepSmemMax, kStepSmemMax);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaFuncSetAttribute"));
   if ((ce = cudaMemsetAsync(h->acc, 0, (size_t)n_cells * kNMom * sizeof(double), s)) != cudaSuccess ||
       (ce = cudaMemsetAsync(h->ncand, 0, (size_t)n_cells * 8, s)) != cudaSuccess ||
@@ -481,8 +496,14 @@ dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double
                        cudaMemcpyHostToDevice, s);
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpyAsync"));
   ce = timed(h, K_INIT,
-             [&] { return launch_init(h->st[0], (int)N, ppc, h->ncf, h->k0(), h->k1(), h->err, s); });
+             [&] { return launch_init(h->P[0], (int)N, ppc, h->ncf, h->k0(), h->k1(), h->err, s); });
   if (ce != cudaSuccess) return bail(cuda_fail(ce, "init"));
+  // Particle p was drawn in cell p / ppc: slot spans of whole cells.
+  std::vector<int> off0((size_t)n_cells + 1);
+  for (int c = 0; c <= n_cells; ++c) off0[c] = c * ppc;
+  ce = cudaMemcpyAsync(h->off[h->ocur], off0.data(), off0.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, s);
+  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpyAsync"));
   st = run_index(h);
   if (st != DSMC_OK) return bail(st);
   ce = cudaStreamSynchronize(s);  // smax0 host buffer must outlive the copy
@@ -573,12 +594,17 @@ dsmc_status dsmc_copy_state(dsmc_handle h, float* y, float* vx, float* vy, float
   dsmc_status s = check_handle(h);
   if (s != DSMC_OK) return s;
   DeviceGuard guard(h->device);
-  const DevState& d = h->st[h->cur];
-  const size_t b = (size_t)h->N * sizeof(float);
+  cudaStream_t st = h->stream();
+  // Unpack the records into four arrays in the idle sort buffer, then copy out.
+  float* tmp = reinterpret_cast<float*>(h->P[h->cur ^ 1]);
+  const size_t n = (size_t)h->N;
+  float* arr[4] = {tmp, tmp + n, tmp + 2 * n, tmp + 3 * n};
+  DSMC_CUDA(launch_unpack(h->P[h->cur], arr[0], arr[1], arr[2], arr[3], (int)h->N, st), "unpack");
   float* dst[4] = {y, vx, vy, vz};
-  const float* src[4] = {d.y, d.vx, d.vy, d.vz};
   for (int k = 0; k < 4; ++k)
-    if (dst[k]) DSMC_CUDA(cudaMemcpyAsync(dst[k], src[k], b, cudaMemcpyDefault, h->stream()), "copy state");
+    if (dst[k])
+      DSMC_CUDA(cudaMemcpyAsync(dst[k], arr[k], n * sizeof(float), cudaMemcpyDefault, st),
+                "copy state");
   return dsmc_sync(h);
 }
 
@@ -608,21 +634,25 @@ dsmc_status dsmc_load_state(dsmc_handle h, const float* y, const float* vx, cons
   if (step < 0) return fail(DSMC_E_INVAL, "step must be >= 0");
   DeviceGuard guard(h->device);
   cudaStream_t st = h->stream();
-  const DevState& d = h->st[h->cur];
-  const size_t b = (size_t)h->N * sizeof(float);
-  DSMC_CUDA(cudaMemcpyAsync(d.y, y, b, cudaMemcpyDefault, st), "load state");
-  DSMC_CUDA(cudaMemcpyAsync(d.vx, vx, b, cudaMemcpyDefault, st), "load state");
-  DSMC_CUDA(cudaMemcpyAsync(d.vy, vy, b, cudaMemcpyDefault, st), "load state");
-  DSMC_CUDA(cudaMemcpyAsync(d.vz, vz, b, cudaMemcpyDefault, st), "load state");
+  float* tmp = reinterpret_cast<float*>(h->P[h->cur ^ 1]);
+  const size_t n = (size_t)h->N;
+  const float* src[4] = {y, vx, vy, vz};
+  for (int k = 0; k < 4; ++k)
+    DSMC_CUDA(cudaMemcpyAsync(tmp + k * n, src[k], n * sizeof(float), cudaMemcpyDefault, st),
+              "load state");
+  DSMC_CUDA(launch_pack(tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, h->P[h->cur], (int)h->N, st),
+            "pack");
   if (smax)
     DSMC_CUDA(cudaMemcpyAsync(h->smax[h->scur], smax, (size_t)h->n_cells * sizeof(float),
                               cudaMemcpyDefault, st),
               "load smax");
-  DSMC_CUDA(launch_clamp_y(d.y, (int)h->N, st), "clamp");
   h->step = step;
+  std::vector<int> host;
+  s = set_uniform_offsets(h, host);
+  if (s != DSMC_OK) return s;
   s = run_index(h);
   if (s != DSMC_OK) return s;
-  return dsmc_sync(h);
+  return dsmc_sync(h);  // also keeps `host` alive until its copy has run
 }
 
 dsmc_status dsmc_get_info(dsmc_handle h, dsmc_info* info) {

@@ -70,12 +70,13 @@ struct StepArgs {
   uint32_t step;
   int sample;
   int collide;
-  int mode;  // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
+  int mode;        // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
+  int count_only;  // only count the cells of the span's slots (sort into cells)
 };
 
 // Dynamic shared memory of one collide/move CTA (byte offsets).
 struct StepSmem {
-  size_t hist, cell_acc, cell_cand, cell_accn, cell_gmax, warps, per_warp, total;
+  size_t hist, cell_acc, cell_cand, cell_accn, cell_gmax, cell_groups, warps, per_warp, total;
 };
 
 __host__ __device__ inline size_t step_align(size_t o, size_t a) { return (o + a - 1) / a * a; }
@@ -92,17 +93,17 @@ __host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int c
   L.cell_accn = o;
   o += (size_t)cps * 8;
   L.cell_gmax = o;
-  o = step_align(o + (size_t)cps * 4, 16);
-  // per warp: vx, vy, vz, owner (cap words each) and 13 x 32 lane accumulators
-  L.per_warp = step_align((size_t)cap * 16 + (size_t)kNMom * 32 * 4, 16);
+  o += (size_t)cps * 4;
+  L.cell_groups = o;  // group prefix of the span's cells (cps + 1) and a counter
+  o = step_align(o + ((size_t)cps + 2) * 4, 16);
+  // per warp: vx, vy, vz, y, owner (cap words each) and 13 x 32 lane accumulators
+  L.per_warp = step_align((size_t)cap * 20 + (size_t)kNMom * 32 * 4, 16);
   L.warps = o;
   o += (size_t)kAWarps * L.per_warp;
   L.total = o;
   return L;
 }
 
-cudaError_t launch_init(const DevState& s, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
-                        int* err, cudaStream_t st);
 cudaError_t launch_move_count(const DevState& s, int N, const SortPlan& sp, int n_cells,
                               float ncf, const MoveArgs& m, int* hist, int* err,
                               cudaStream_t st);
@@ -111,17 +112,22 @@ cudaError_t launch_cell_offsets(const int* count, int n_cells, int* offset, cuda
 cudaError_t launch_scatter(const DevState& from, const DevState& to, int N, const SortPlan& sp,
                            int n_cells, float ncf, const int* hist, const int* offset,
                            int* err, cudaStream_t st);
-cudaError_t launch_clamp_y(float* y, int N, cudaStream_t st);
 cudaError_t set_kernel_smem_limits(size_t sort_bytes);
 
-cudaError_t launch_collide_move(const DevState& s, const int* off, const float* smax_in,
+cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 float* smax_out, unsigned long long* ncand,
                                 unsigned long long* nacc, double* acc, int* hist,
                                 const StepArgs& a, int n_spans, int* err, cudaStream_t st);
 int scatter_spans_warps(int n_cells);
-cudaError_t launch_scatter_spans(const DevState& from, const DevState& to, const int* off_cur,
+cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur,
                                  const int* off_new, const int* hist, int n_cells, int cps,
                                  int n_spans, float ncf, int N, int* err, cudaStream_t st);
+cudaError_t launch_unpack(const float4* P, float* y, float* vx, float* vy, float* vz, int N,
+                          cudaStream_t st);
+cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const float* vz,
+                        float4* P, int N, cudaStream_t st);
+cudaError_t launch_init(float4* P, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
+                        int* err, cudaStream_t st);
 cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes);
 
 // Sets the message dsmc_last_error() returns on the calling thread.

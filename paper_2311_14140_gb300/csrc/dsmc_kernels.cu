@@ -27,15 +27,14 @@ namespace dsmc {
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
-// Initial state.
-__global__ void k_init(float* __restrict__ y, float* __restrict__ vx, float* __restrict__ vy,
-                       float* __restrict__ vz, int N, int ppc, float ncf, uint32_t k0,
+// Initial state, as float4 records (y, vx, vy, vz).
+__global__ void k_init(float4* __restrict__ P, int N, int ppc, float ncf, uint32_t k0,
                        uint32_t k1, int* __restrict__ err) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
     const int c = p / ppc;
     const uint32_t c3 = kStreamInit << 24;
     U4 w = philox((uint32_t)p, 0u, 0u, c3, k0, k1);
-    y[p] = fdiv(fadd((float)c, u01(w.x)), ncf);
+    const float y = fdiv(fadd((float)c, u01(w.x)), ncf);
     float z[3];
     int have = 0;
     for (int a = 0; a < kNormalAttempts && have < 3; ++a) {
@@ -50,9 +49,7 @@ __global__ void k_init(float* __restrict__ y, float* __restrict__ vx, float* __r
       atomicOr(err, kErrNormals);
       for (int i = have; i < 3; ++i) z[i] = 0.0f;
     }
-    vx[p] = z[0];
-    vy[p] = z[1];
-    vz[p] = z[2];
+    P[p] = make_float4(y, z[0], z[1], z[2]);
   }
 }
 
@@ -212,22 +209,14 @@ __global__ void k_scatter(const float* __restrict__ y, const float* __restrict__
   }
 }
 
-__global__ void k_clamp_y(float* __restrict__ y, int N) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
-    const float v = y[p];
-    y[p] = (v >= 0.0f) ? ((v <= 1.0f) ? v : 1.0f) : 0.0f;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Launchers.
 
-cudaError_t launch_init(const DevState& s, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
+cudaError_t launch_init(float4* P, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
                         int* err, cudaStream_t st) {
   const int threads = 256;
   const int blocks = (N + threads - 1) / threads;
-  k_init<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(s.y, s.vx, s.vy, s.vz, N, ppc, ncf, k0,
-                                                      k1, err);
+  k_init<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(P, N, ppc, ncf, k0, k1, err);
   return cudaGetLastError();
 }
 
@@ -260,13 +249,6 @@ cudaError_t launch_scatter(const DevState& from, const DevState& to, int N, cons
   k_scatter<<<blocks, sp.wpb * 32, smem, st>>>(from.y, from.vx, from.vy, from.vz, to.y, to.vx,
                                                to.vy, to.vz, N, sp.span, sp.n_warps, n_cells,
                                                ncf, hist, offset, err);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_clamp_y(float* y, int N, cudaStream_t st) {
-  const int threads = 256;
-  const int blocks = (N + threads - 1) / threads;
-  k_clamp_y<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(y, N);
   return cudaGetLastError();
 }
 

@@ -1,24 +1,30 @@
 // dsmc_step.cu -- the two state passes of one DSMC step (Bird's method, which the
-// paper cites for its micro model; problem of Sec. 2.1, units of Eq. 5):
+// paper cites for its micro model; problem of Sec. 2.1, units of Eq. 5).
 //
-//   k_collide_move   one CTA per span of consecutive cells.  Each warp takes the
-//                    span's collision groups in turn, stages a group's velocities in
-//                    shared memory and
-//                      1. adds the group's moment sums taken before the collisions,
-//                      2. draws every NTC candidate's pair, acceptance threshold and
-//                         scattering direction up front (32 candidates at a time,
-//                         one per lane), then applies the candidates in conflict-free
-//                         rounds that reproduce the sequential order exactly,
-//                      3. adds the moment sums taken after the collisions,
-//                      4. moves each particle (body force, diffuse walls) and counts
-//                         its new cell into the CTA's histogram,
-//                    writing the moved state back in place.  The histogram becomes the
-//                    span's row of the sort matrix; per-cell (sigma g)_max, collision
-//                    counters and moment sums are written by the one CTA that owns
-//                    the cell.
-//   k_scatter_spans  one warp per span: re-reads the moved state in slot order and
-//                    scatters it, stably, into the other buffer, using the span's row
-//                    of the prefix-summed matrix plus the new cell offsets.
+// The resident particle state is an array of float4 records (y, vx, vy, vz): one
+// 16-byte load or store moves a whole particle, so the sort's scattered writes cost
+// one L2 sector per particle instead of four.
+//
+//   k_collide_move   one CTA per span of consecutive cells.  Its warps take the span's
+//                    collision groups one after another (a shared counter hands them
+//                    out) and for each group
+//                      1. load the group's records, keep them in shared memory and add
+//                         their moment sums before the collisions,
+//                      2. draw every NTC candidate's pair, acceptance threshold and
+//                         scattering direction up front (32 candidates at a time, one
+//                         per lane), then apply the candidates in conflict-free rounds
+//                         that reproduce the sequential order exactly,
+//                      3. per particle: add the moment sums after the collisions, fly
+//                         with the body force and diffuse walls, store the record back
+//                         in place and count its new cell in the CTA's histogram.
+//                    The histogram becomes the span's row of the sort matrix.  Per-cell
+//                    (sigma g)_max, collision counters and moment sums are written by
+//                    the one CTA that owns the cell.  With `count_only` the pass just
+//                    counts cells of the span's slots (the sort into cells at creation
+//                    and after a state load).
+//   k_scatter_spans  one warp per span: re-reads the records in slot order, 16 per lane
+//                    in flight, and scatters them stably into the other buffer from the
+//                    span's row of the prefix-summed matrix plus the new cell offsets.
 //
 // Between them, k_scan_hist and k_cell_offsets (dsmc_kernels.cu) turn the matrix into
 // per-span bases and the new cell offsets.
@@ -32,7 +38,7 @@ namespace dsmc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kFlushEvery = 4;  // groups per lane-accumulator flush (bounds FP32 chains)
+constexpr int kFlushEvery = 4;  // group samples per lane-accumulator flush
 
 // Scattering direction from one polar attempt (Marsaglia 1972): (a0, a1) uniform in
 // the unit disc gives n = (2 a0 sqrt(1-s), 2 a1 sqrt(1-s), 1 - 2 s), uniform on the
@@ -50,33 +56,52 @@ __device__ __forceinline__ bool sphere(uint32_t w0, uint32_t w1, float& nx, floa
   return true;
 }
 
-// Add one group's 13 raw moment sums (products in binary32, as the oracle forms them)
-// to this lane's column of the warp's accumulators.
-__device__ __forceinline__ void sample_group(float* lacc, const float* sx, const float* sy,
-                                             const float* sz, int gn, int lane) {
-  float m[kNMom];
-#pragma unroll
-  for (int k = 0; k < kNMom; ++k) m[k] = 0.0f;
-  for (int i = lane; i < gn; i += 32) {
-    const float x = sx[i], y = sy[i], z = sz[i];
-    const float xx = fmul(x, x), yy = fmul(y, y), zz = fmul(z, z);
-    const float v2 = fadd(fadd(xx, yy), zz);
-    m[0] += 1.0f;
-    m[1] += x;
-    m[2] += y;
-    m[3] += z;
-    m[4] += xx;
-    m[5] += yy;
-    m[6] += zz;
-    m[7] += fmul(x, y);
-    m[8] += fmul(x, z);
-    m[9] += fmul(y, z);
-    m[10] += fmul(x, v2);
-    m[11] += fmul(y, v2);
-    m[12] += fmul(z, v2);
+// The 13 raw moments of one particle (products in binary32, formed as the oracle forms
+// them), added in pairs with packed binary32 arithmetic.
+struct Moments {
+  float2 a, b, c, d, e;  // (1, vx) (vy, vz) (vx2, vy2) (vz2, vxvy) (vxvz, vyvz)
+  float2 g;              // (vx v2, vy v2)
+  float h;               // vz v2
+  __device__ __forceinline__ void zero() {
+    a = b = c = d = e = g = make_float2(0.0f, 0.0f);
+    h = 0.0f;
   }
+  __device__ __forceinline__ void add(float x, float y, float z) {
+    const float2 xy = make_float2(x, y);
+    const float2 sq = __fmul2_rn(xy, xy);
+    const float zz = fmul(z, z);
+    const float v2 = fadd(fadd(sq.x, sq.y), zz);
+    a = __fadd2_rn(a, make_float2(1.0f, x));
+    b = __fadd2_rn(b, make_float2(y, z));
+    c = __fadd2_rn(c, sq);
+    d = __fadd2_rn(d, make_float2(zz, fmul(x, y)));
+    e = __fadd2_rn(e, __fmul2_rn(make_float2(x, y), make_float2(z, z)));
+    g = __fadd2_rn(g, __fmul2_rn(xy, make_float2(v2, v2)));
+    h = fadd(h, fmul(z, v2));
+  }
+  __device__ __forceinline__ float get(int k) const {
+    switch (k) {
+      case 0: return a.x;
+      case 1: return a.y;
+      case 2: return b.x;
+      case 3: return b.y;
+      case 4: return c.x;
+      case 5: return c.y;
+      case 6: return d.x;
+      case 7: return d.y;
+      case 8: return e.x;
+      case 9: return e.y;
+      case 10: return g.x;
+      case 11: return g.y;
+      default: return h;
+    }
+  }
+};
+
+// Add a group's partial sums into this lane's column of the warp accumulators.
+__device__ __forceinline__ void add_to_lanes(float* lacc, const Moments& m, int lane) {
 #pragma unroll
-  for (int k = 0; k < kNMom; ++k) lacc[k * 32 + lane] += m[k];
+  for (int k = 0; k < kNMom; ++k) lacc[k * 32 + lane] += m.get(k);
 }
 
 // Warp sum of the lane accumulators, added (times 1/2: half a sample before and half
@@ -92,14 +117,30 @@ __device__ __forceinline__ void flush_moments(float* lacc, double* cell_acc, int
   }
 }
 
+// Per-cell results a warp gathered, added into the CTA's slots of that cell.
+__device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
+                                           unsigned long long accn, unsigned* cgmax,
+                                           unsigned long long* ccand,
+                                           unsigned long long* caccn, int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
+    accn += __shfl_xor_sync(kFull, accn, o);
+  }
+  if (lane == 0) {  // cand is the same on every lane: the sum of the groups' M
+    atomicMax(cgmax, __float_as_uint(gmax));  // gmax >= 0: bits order as values
+    atomicAdd(ccand, cand);
+    atomicAdd(caccn, accn);
+  }
+}
+
 }  // namespace
 
 // Modes of the collision model: 0 hard spheres, 1 VHS with 0.5 < omega < 1,
 // 2 omega = 1 (sigma g independent of g).
 template <int kMode>
 __global__ void __launch_bounds__(kAWarps * 32, 2)
-    k_collide_move(float* __restrict__ y, float* __restrict__ vx, float* __restrict__ vy,
-                   float* __restrict__ vz, const int* __restrict__ off,
+    k_collide_move(float4* __restrict__ P, const int* __restrict__ off,
                    const float* __restrict__ smax_in, float* __restrict__ smax_out,
                    unsigned long long* __restrict__ ncand, unsigned long long* __restrict__ nacc,
                    double* __restrict__ acc, int* __restrict__ hist, StepArgs a,
@@ -115,182 +156,229 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
   unsigned long long* ccand = reinterpret_cast<unsigned long long*>(smem + L.cell_cand);
   unsigned long long* caccn = reinterpret_cast<unsigned long long*>(smem + L.cell_accn);
   unsigned* cgmax = reinterpret_cast<unsigned*>(smem + L.cell_gmax);
+  int* gfirst = reinterpret_cast<int*>(smem + L.cell_groups);  // cps + 1 group prefix
+  int* next_group = gfirst + cps + 1;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   unsigned char* wmem = smem + L.warps + (size_t)wib * L.per_warp;
   float* sx = reinterpret_cast<float*>(wmem);
   float* sy = sx + cap;
   float* sz = sy + cap;
-  int* own = reinterpret_cast<int*>(sz + cap);
+  float* spos = sz + cap;
+  int* own = reinterpret_cast<int*>(spos + cap);
   float* lacc = reinterpret_cast<float*>(own + cap);  // kNMom x 32
 
   const int span = blockIdx.x;
   const int c0 = span * cps;
   const int c1 = min(c0 + cps, n_cells);
+  const unsigned lt = (1u << lane) - 1u;
   for (int i = threadIdx.x; i < n_cells; i += blockDim.x) h[i] = 0;
+
+  if (a.count_only) {  // sort into cells: count the cells of the span's slots
+    __syncthreads();
+    const int b0 = off[c0], b1 = off[c1];
+    for (int base = b0 + wib * 32; base < b1; base += blockDim.x) {
+      const int p = base + lane;
+      const int cell = (p < b1) ? cell_of(P[p].x, n_cells, a.ncf) : -1;
+      const unsigned peers = __match_any_sync(kFull, cell);
+      if (cell >= 0 && (peers & lt) == 0) atomicAdd(&h[cell], __popc(peers));
+    }
+    __syncthreads();
+    int* row = hist + (size_t)span * n_cells;
+    for (int i = threadIdx.x; i < n_cells; i += blockDim.x) row[i] = h[i];
+    return;
+  }
+
   for (int i = threadIdx.x; i < cps * kNMom; i += blockDim.x) cacc[i] = 0.0;
   for (int i = threadIdx.x; i < cps; i += blockDim.x) {
     ccand[i] = 0;
     caccn[i] = 0;
     cgmax[i] = 0u;
   }
+  if (threadIdx.x == 0) {
+    int q = 0;
+    for (int c = c0; c < c1; ++c) {
+      gfirst[c - c0] = q;
+      q += group_count(off[c + 1] - off[c], G);
+    }
+    gfirst[c1 - c0] = q;
+    *next_group = 0;
+  }
   for (int k = 0; k < kNMom; ++k) lacc[k * 32 + lane] = 0.0f;
   __syncthreads();
+  const int n_groups = gfirst[c1 - c0];
 
   bool bad_bounce = false, sphere_fail = false, cand_fail = false;
-  const unsigned lt = (1u << lane) - 1u;
-  int qbase = 0;  // groups of the span before cell c
-  for (int c = c0; c < c1; ++c) {
+  int cur = -1;  // local cell the warp is gathering results for
+  float gmax = 0.0f;
+  unsigned long long lcand = 0, laccn = 0;
+  int pending = 0;  // group samples in the lane accumulators
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(next_group, 1);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= n_groups) break;
+    int lc = 0;
+    while (gfirst[lc + 1] <= q) ++lc;
+    if (lc != cur) {  // results so far belong to another cell
+      if (cur >= 0) {
+        if (a.sample && pending > 0) flush_moments(lacc, cacc + (size_t)cur * kNMom, lane);
+        flush_cell(gmax, lcand, laccn, &cgmax[cur], &ccand[cur], &caccn[cur], lane);
+      }
+      cur = lc;
+      gmax = 0.0f;
+      lcand = 0;
+      laccn = 0;
+      pending = 0;
+    }
+    const int c = c0 + lc;
+    const int gi = q - gfirst[lc];
     const int start = off[c];
     const int nc = off[c + 1] - start;
-    const int ng = group_count(nc, G);
+    const int ng = gfirst[lc + 1] - gfirst[lc];
+    const int gs = start + gi * G;
+    const int gn = (gi == ng - 1) ? nc - gi * G : G;
     const float smax = smax_in[c];
-    float gmax = 0.0f;
-    unsigned long long lcand = 0, laccn = 0;
-    int pending_flush = 0;
-    // This warp takes the groups q of the span with q = wib (mod kAWarps).
-    const int gi0 = ((wib - qbase) % kAWarps + kAWarps) % kAWarps;
-    for (int gi = gi0; gi < ng; gi += kAWarps) {
-      const int gs = start + gi * G;
-      const int gn = (gi == ng - 1) ? nc - gi * G : G;
-      for (int i = lane; i < gn; i += 32) {
-        sx[i] = vx[gs + i];
-        sy[i] = vy[gs + i];
-        sz[i] = vz[gs + i];
-        own[i] = INT_MAX;
-      }
-      __syncwarp();
-      if (a.sample) sample_group(lacc, sx, sy, sz, gn, lane);
 
-      if (a.collide && gn >= 2) {
-        const uint32_t c3 = (kStreamColl << 24) | ((uint32_t)gi << 4);
-        const float t1 = fmul((float)(gn - 1), (float)nc);
-        const float mf = fmul(fmul(t1, a.coef), smax);
-        const float fl = floorf(mf);
-        const float frac = fsub(mf, fl);
-        uint32_t M = (uint32_t)fl;
-        const U4 r = philox(0xffffffffu, (uint32_t)c, a.step, c3, a.k0, a.k1);
-        if (u01(r.x) < frac) M += 1;
-        if (!(mf <= kMaxCandidates)) {
-          M = 0;
-          cand_fail = true;
+    // 1. Stage the group; moments before the collisions.
+    {
+      Moments m;
+      m.zero();
+      for (int i = lane; i < gn; i += 32) {
+        const float4 r = P[gs + i];
+        spos[i] = r.x;
+        sx[i] = r.y;
+        sy[i] = r.z;
+        sz[i] = r.w;
+        own[i] = INT_MAX;
+        if (a.sample) m.add(r.y, r.z, r.w);
+      }
+      if (a.sample) add_to_lanes(lacc, m, lane);
+    }
+    __syncwarp();
+
+    // 2. NTC candidates of the group.
+    if (a.collide && gn >= 2) {
+      const uint32_t c3 = (kStreamColl << 24) | ((uint32_t)gi << 4);
+      const float t1 = fmul((float)(gn - 1), (float)nc);
+      const float mf = fmul(fmul(t1, a.coef), smax);
+      const float fl = floorf(mf);
+      const float frac = fsub(mf, fl);
+      uint32_t M = (uint32_t)fl;
+      const U4 r = philox(0xffffffffu, (uint32_t)c, a.step, c3, a.k0, a.k1);
+      if (u01(r.x) < frac) M += 1;
+      if (!(mf <= kMaxCandidates)) {
+        M = 0;
+        cand_fail = true;
+      }
+      lcand += M;
+      for (uint32_t kb = 0; kb < M; kb += 32) {
+        const uint32_t k = kb + (uint32_t)lane;
+        bool pend = k < M;
+        int i = 0, j = 0;
+        float thr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
+        bool have_dir = false;
+        if (pend) {
+          const U4 w = philox(k, (uint32_t)c, a.step, c3, a.k0, a.k1);
+          i = (int)__umulhi(w.x, (uint32_t)gn);
+          j = (int)__umulhi(w.y, (uint32_t)(gn - 1));
+          j += (j >= i) ? 1 : 0;
+          const float us = fmul(u01(w.z), smax);
+          if (kMode == 0)
+            thr = us;
+          else if (kMode == 1)
+            thr = exp32(fmul(a.vinv, ln32(fdiv(us, a.cvhs))));
+          else
+            thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
+          const U4 d = philox(k, (uint32_t)c, a.step, c3 | 1u, a.k0, a.k1);
+          have_dir = sphere(d.x, d.y, nx, ny, nz) || sphere(d.z, d.w, nx, ny, nz);
         }
-        lcand += M;
-        for (uint32_t kb = 0; kb < M; kb += 32) {
-          const uint32_t k = kb + (uint32_t)lane;
-          bool pend = k < M;
-          int i = 0, j = 0;
-          float thr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
-          bool have_dir = false;
-          if (pend) {
-            const U4 w = philox(k, (uint32_t)c, a.step, c3, a.k0, a.k1);
-            i = (int)__umulhi(w.x, (uint32_t)gn);
-            j = (int)__umulhi(w.y, (uint32_t)(gn - 1));
-            j += (j >= i) ? 1 : 0;
-            const float us = fmul(u01(w.z), smax);
-            if (kMode == 0)
-              thr = us;
-            else if (kMode == 1)
-              thr = exp32(fmul(a.vinv, ln32(fdiv(us, a.cvhs))));
-            else
-              thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
-            const U4 d = philox(k, (uint32_t)c, a.step, c3 | 1u, a.k0, a.k1);
+        if (__any_sync(kFull, pend && !have_dir)) {
+          // Rare: both attempts of the first draw fell outside the disc.
+          for (int at = 2; at < kNormalAttempts && pend && !have_dir; at += 2) {
+            const U4 d = philox(k, (uint32_t)c, a.step, c3 | (1u + (uint32_t)(at >> 1)),
+                                a.k0, a.k1);
             have_dir = sphere(d.x, d.y, nx, ny, nz) || sphere(d.z, d.w, nx, ny, nz);
           }
-          if (__any_sync(kFull, pend && !have_dir)) {
-            // Rare: both attempts of the first draw fell outside the disc.
-            for (int at = 2; at < kNormalAttempts && pend && !have_dir; at += 2) {
-              const U4 d = philox(k, (uint32_t)c, a.step, c3 | (1u + (uint32_t)(at >> 1)),
-                                  a.k0, a.k1);
-              have_dir = sphere(d.x, d.y, nx, ny, nz) || sphere(d.z, d.w, nx, ny, nz);
-            }
-          }
-          while (__any_sync(kFull, pend)) {
-            if (pend) {
-              atomicMin(&own[i], lane);
-              atomicMin(&own[j], lane);
-            }
-            __syncwarp();
-            const bool ready = pend && own[i] == lane && own[j] == lane;
-            __syncwarp();
-            if (pend) {
-              own[i] = INT_MAX;
-              own[j] = INT_MAX;
-            }
-            if (ready) {
-              const float xi = sx[i], yi = sy[i], zi = sz[i];
-              const float xj = sx[j], yj = sy[j], zj = sz[j];
-              const float gx = fsub(xi, xj), gy = fsub(yi, yj), gz = fsub(zi, zj);
-              const float g = fsqrt(fadd(fadd(fmul(gx, gx), fmul(gy, gy)), fmul(gz, gz)));
-              gmax = fmaxf(gmax, g);
-              if (g > thr) {
-                if (have_dir) {
-                  const float hg = fmul(0.5f, g);
-                  const float cx = fmul(fadd(xi, xj), 0.5f);
-                  const float cy = fmul(fadd(yi, yj), 0.5f);
-                  const float cz = fmul(fadd(zi, zj), 0.5f);
-                  const float dx = fmul(hg, nx), dy = fmul(hg, ny), dz = fmul(hg, nz);
-                  sx[i] = fadd(cx, dx);
-                  sy[i] = fadd(cy, dy);
-                  sz[i] = fadd(cz, dz);
-                  sx[j] = fsub(cx, dx);
-                  sy[j] = fsub(cy, dy);
-                  sz[j] = fsub(cz, dz);
-                  laccn += 1;
-                } else {
-                  sphere_fail = true;
-                }
-              }
-              pend = false;
-            }
-            __syncwarp();
-          }
         }
-      }
-      __syncwarp();
-      if (a.sample) {
-        sample_group(lacc, sx, sy, sz, gn, lane);
-        if (++pending_flush == kFlushEvery) {
+        while (__any_sync(kFull, pend)) {
+          if (pend) {
+            atomicMin(&own[i], lane);
+            atomicMin(&own[j], lane);
+          }
           __syncwarp();
-          flush_moments(lacc, cacc + (size_t)(c - c0) * kNMom, lane);
-          pending_flush = 0;
+          const bool ready = pend && own[i] == lane && own[j] == lane;
+          __syncwarp();
+          if (pend) {
+            own[i] = INT_MAX;
+            own[j] = INT_MAX;
+          }
+          if (ready) {
+            const float xi = sx[i], yi = sy[i], zi = sz[i];
+            const float xj = sx[j], yj = sy[j], zj = sz[j];
+            const float gx = fsub(xi, xj), gy = fsub(yi, yj), gz = fsub(zi, zj);
+            const float g = fsqrt(fadd(fadd(fmul(gx, gx), fmul(gy, gy)), fmul(gz, gz)));
+            gmax = fmaxf(gmax, g);
+            if (g > thr) {
+              if (have_dir) {
+                const float hg = fmul(0.5f, g);
+                const float cx = fmul(fadd(xi, xj), 0.5f);
+                const float cy = fmul(fadd(yi, yj), 0.5f);
+                const float cz = fmul(fadd(zi, zj), 0.5f);
+                const float dx = fmul(hg, nx), dy = fmul(hg, ny), dz = fmul(hg, nz);
+                sx[i] = fadd(cx, dx);
+                sy[i] = fadd(cy, dy);
+                sz[i] = fadd(cz, dz);
+                sx[j] = fsub(cx, dx);
+                sy[j] = fsub(cy, dy);
+                sz[j] = fsub(cz, dz);
+                laccn += 1;
+              } else {
+                sphere_fail = true;
+              }
+            }
+            pend = false;
+          }
+          __syncwarp();
         }
       }
-      // Free flight and the count of the new cell; the state goes back in place.
+    }
+    __syncwarp();
+
+    // 3. Moments after the collisions, free flight, store, count the new cell.
+    {
+      Moments m;
+      m.zero();
       for (int b = 0; b < gn; b += 32) {
         const int i = b + lane;
         const bool act = i < gn;
         int cell = -1;
         if (act) {
           const int p = gs + i;
-          float yy = y[p], xx = sx[i], uy = sy[i], zz = sz[i];
+          float yy = spos[i], xx = sx[i], uy = sy[i], zz = sz[i];
+          if (a.sample) m.add(xx, uy, zz);
           if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, a.step, (uint32_t)p)) bad_bounce = true;
-          y[p] = yy;
-          vx[p] = xx;
-          vy[p] = uy;
-          vz[p] = zz;
+          P[p] = make_float4(yy, xx, uy, zz);
           cell = cell_of(yy, n_cells, a.ncf);
         }
         const unsigned peers = __match_any_sync(kFull, cell);
         if (act && (peers & lt) == 0) atomicAdd(&h[cell], __popc(peers));
       }
-      __syncwarp();
+      if (a.sample) {
+        add_to_lanes(lacc, m, lane);
+        pending += 2;
+        if (pending >= 2 * kFlushEvery) {
+          __syncwarp();
+          flush_moments(lacc, cacc + (size_t)cur * kNMom, lane);
+          pending = 0;
+        }
+      }
     }
-    if (a.sample && pending_flush > 0) {
-      __syncwarp();
-      flush_moments(lacc, cacc + (size_t)(c - c0) * kNMom, lane);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
-      laccn += __shfl_xor_sync(kFull, laccn, o);
-    }
-    if (lane == 0) {  // lcand is the same on every lane: the sum of the groups' M
-      atomicMax(&cgmax[c - c0], __float_as_uint(gmax));  // gmax >= 0: bits order as values
-      atomicAdd(&ccand[c - c0], lcand);
-      atomicAdd(&caccn[c - c0], laccn);
-    }
-    qbase += ng;
+    __syncwarp();
+  }
+  if (cur >= 0) {
+    if (a.sample && pending > 0) flush_moments(lacc, cacc + (size_t)cur * kNMom, lane);
+    flush_cell(gmax, lcand, laccn, &cgmax[cur], &ccand[cur], &caccn[cur], lane);
   }
   if (bad_bounce) atomicOr(err, kErrBounces);
   if (sphere_fail) atomicOr(err, kErrSphere);
@@ -311,17 +399,14 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
   }
 }
 
-// One warp per span: stable scatter of the span's slots into the other buffer.  Eight
-// groups of 32 slots are loaded before any is placed, so each lane keeps 32 loads in
-// flight.
+// One warp per span: stable scatter of the span's records into the other buffer.  Each
+// lane keeps kUnroll records in flight before any of them is placed.
 __global__ void __launch_bounds__(kBWarpsMax * 32)
-    k_scatter_spans(const float* __restrict__ y, const float* __restrict__ vx,
-                    const float* __restrict__ vy, const float* __restrict__ vz,
-                    float* __restrict__ y2, float* __restrict__ vx2, float* __restrict__ vy2,
-                    float* __restrict__ vz2, const int* __restrict__ off_cur,
-                    const int* __restrict__ off_new, const int* __restrict__ hist, int n_cells,
-                    int cps, int n_spans, float ncf, int N, int* __restrict__ err) {
-  constexpr int kUnroll = 8;
+    k_scatter_spans(const float4* __restrict__ P, float4* __restrict__ P2,
+                    const int* __restrict__ off_cur, const int* __restrict__ off_new,
+                    const int* __restrict__ hist, int n_cells, int cps, int n_spans, float ncf,
+                    int N, int* __restrict__ err) {
+  constexpr int kUnroll = 16;
   extern __shared__ int sh_run[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -338,22 +423,17 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   const unsigned lt = (1u << lane) - 1u;
   bool bad = false;
   for (int base = b0; base < b1; base += 32 * kUnroll) {
-    float ry[kUnroll], rx[kUnroll], rv[kUnroll], rz[kUnroll];
+    float4 rec[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int p = base + u * 32 + lane;
-      if (p < b1) {
-        ry[u] = y[p];
-        rx[u] = vx[p];
-        rv[u] = vy[p];
-        rz[u] = vz[p];
-      }
+      if (p < b1) rec[u] = P[p];
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int p = base + u * 32 + lane;
       const bool act = p < b1;
-      const int cell = act ? cell_of(ry[u], n_cells, ncf) : -1;
+      const int cell = act ? cell_of(rec[u].x, n_cells, ncf) : -1;
       const unsigned peers = __match_any_sync(kFull, cell);
       const int first = act ? run[cell] : 0;
       __syncwarp();
@@ -361,23 +441,43 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
       __syncwarp();
       if (act) {
         const int d = first + __popc(peers & lt);
-        if (d >= 0 && d < N) {
-          y2[d] = ry[u];
-          vx2[d] = rx[u];
-          vy2[d] = rv[u];
-          vz2[d] = rz[u];
-        } else {
+        if (d >= 0 && d < N)
+          P2[d] = rec[u];
+        else
           bad = true;
-        }
       }
     }
   }
   if (bad) atomicOr(err, kErrSort);
 }
 
+// Records <-> four arrays (y, vx, vy, vz), for the state accessors.
+__global__ void k_unpack(const float4* __restrict__ P, float* __restrict__ y,
+                         float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
+                         int N) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    const float4 r = P[p];
+    y[p] = r.x;
+    vx[p] = r.y;
+    vy[p] = r.z;
+    vz[p] = r.w;
+  }
+}
+
+// Pack four arrays into records; y is moved onto the nearest wall if outside [0, 1].
+__global__ void k_pack(const float* __restrict__ y, const float* __restrict__ vx,
+                       const float* __restrict__ vy, const float* __restrict__ vz,
+                       float4* __restrict__ P, int N) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    const float v = y[p];
+    const float yc = (v >= 0.0f) ? ((v <= 1.0f) ? v : 1.0f) : 0.0f;
+    P[p] = make_float4(yc, vx[p], vy[p], vz[p]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_collide_move(const DevState& s, const int* off, const float* smax_in,
+cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 float* smax_out, unsigned long long* ncand,
                                 unsigned long long* nacc, double* acc, int* hist,
                                 const StepArgs& a, int n_spans, int* err, cudaStream_t st) {
@@ -385,19 +485,16 @@ cudaError_t launch_collide_move(const DevState& s, const int* off, const float* 
   const dim3 block(kAWarps * 32);
   switch (a.mode) {
     case 0:
-      k_collide_move<0><<<n_spans, block, L.total, st>>>(s.y, s.vx, s.vy, s.vz, off, smax_in,
-                                                          smax_out, ncand, nacc, acc, hist, a,
-                                                          err);
+      k_collide_move<0><<<n_spans, block, L.total, st>>>(P, off, smax_in, smax_out, ncand, nacc,
+                                                          acc, hist, a, err);
       break;
     case 1:
-      k_collide_move<1><<<n_spans, block, L.total, st>>>(s.y, s.vx, s.vy, s.vz, off, smax_in,
-                                                          smax_out, ncand, nacc, acc, hist, a,
-                                                          err);
+      k_collide_move<1><<<n_spans, block, L.total, st>>>(P, off, smax_in, smax_out, ncand, nacc,
+                                                          acc, hist, a, err);
       break;
     default:
-      k_collide_move<2><<<n_spans, block, L.total, st>>>(s.y, s.vx, s.vy, s.vz, off, smax_in,
-                                                          smax_out, ncand, nacc, acc, hist, a,
-                                                          err);
+      k_collide_move<2><<<n_spans, block, L.total, st>>>(P, off, smax_in, smax_out, ncand, nacc,
+                                                          acc, hist, a, err);
   }
   return cudaGetLastError();
 }
@@ -408,15 +505,28 @@ int scatter_spans_warps(int n_cells) {
   return w < 1 ? 1 : (int)w;
 }
 
-cudaError_t launch_scatter_spans(const DevState& from, const DevState& to, const int* off_cur,
+cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur,
                                  const int* off_new, const int* hist, int n_cells, int cps,
                                  int n_spans, float ncf, int N, int* err, cudaStream_t st) {
   const int wpb = scatter_spans_warps(n_cells);
   const size_t smem = (size_t)wpb * n_cells * sizeof(int);
   const int blocks = (n_spans + wpb - 1) / wpb;
-  k_scatter_spans<<<blocks, wpb * 32, smem, st>>>(from.y, from.vx, from.vy, from.vz, to.y,
-                                                     to.vx, to.vy, to.vz, off_cur, off_new,
-                                                     hist, n_cells, cps, n_spans, ncf, N, err);
+  k_scatter_spans<<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, n_cells, cps,
+                                                 n_spans, ncf, N, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const float4* P, float* y, float* vx, float* vy, float* vz, int N,
+                          cudaStream_t st) {
+  const int blocks = (N + 255) / 256;
+  k_unpack<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(P, y, vx, vy, vz, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const float* vz,
+                        float4* P, int N, cudaStream_t st) {
+  const int blocks = (N + 255) / 256;
+  k_pack<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(y, vx, vy, vz, P, N);
   return cudaGetLastError();
 }
 
