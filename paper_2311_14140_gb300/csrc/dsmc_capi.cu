@@ -368,6 +368,7 @@ dsmc_status read_error_word(dsmc_sim* h) {
     if (v & kErrSphere) what += " scattering-attempts";
     if (v & kErrCandidates) what += " candidate-count";
     if (v & kErrSort) what += " sort-destination";
+    if (v & kErrCopyTimeout) what += " bulk-copy-timeout";
     return fail(DSMC_E_DEVICE_LIMIT, "device limit reached:" + what);
   }
   return DSMC_OK;

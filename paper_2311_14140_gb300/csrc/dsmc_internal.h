@@ -26,6 +26,7 @@ constexpr int kErrBounces = 2;  // wall bounce limit
 constexpr int kErrSphere = 4;   // post-collision direction attempts ran out
 constexpr int kErrCandidates = 8;  // a group's candidate count exceeded kMaxCandidates
 constexpr int kErrSort = 16;       // a scatter destination fell outside [0, N)
+constexpr int kErrCopyTimeout = 32;  // a bulk copy into shared memory did not complete
 
 // Largest NTC candidate count of one group in one step (about 80 on the largest
 // workload): anything above means corrupted (sigma g)_max and is skipped.
@@ -77,6 +78,7 @@ struct StepArgs {
 // Dynamic shared memory of one collide/move CTA (byte offsets).
 struct StepSmem {
   size_t hist, cell_acc, cell_cand, cell_accn, cell_gmax, cell_groups, warps, per_warp, total;
+  size_t w_rec, w_own, w_sum, w_bar;  // offsets inside one warp's area
 };
 
 __host__ __device__ inline size_t step_align(size_t o, size_t a) { return (o + a - 1) / a * a; }
@@ -95,15 +97,30 @@ __host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int c
   L.cell_gmax = o;
   o += (size_t)cps * 4;
   L.cell_groups = o;  // group prefix of the span's cells (cps + 1) and a counter
-  o = step_align(o + ((size_t)cps + 2) * 4, 16);
-  // per warp: vx, vy, vz, y, owner (cap words each) and 13 x 32 lane accumulators
-  L.per_warp = step_align((size_t)cap * 20 + (size_t)kNMom * 32 * 4, 16);
+  o = step_align(o + ((size_t)cps + 2) * 4, 128);
+  // per warp: the group's records (cap float4, written by a bulk copy), an owner word
+  // per particle, 13 binary64 moment sums of the current cell, and an mbarrier
+  size_t w = 0;
+  L.w_rec = w;
+  w += (size_t)cap * 16;
+  L.w_own = w;
+  w = step_align(w + (size_t)cap * 4, 8);
+  L.w_sum = w;
+  w += (size_t)kNMom * 8;
+  L.w_bar = w;
+  w += 8;
+  L.per_warp = step_align(w, 128);
   L.warps = o;
   o += (size_t)kAWarps * L.per_warp;
   L.total = o;
   return L;
 }
 
+cudaError_t launch_init(float4* P, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
+                        int* err, cudaStream_t st);
+
+// Sort into cells over fixed spans of slots, four separate arrays (the
+// allocation-free sort); the prefix kernels are also used by every step.
 cudaError_t launch_move_count(const DevState& s, int N, const SortPlan& sp, int n_cells,
                               float ncf, const MoveArgs& m, int* hist, int* err,
                               cudaStream_t st);
@@ -114,6 +131,7 @@ cudaError_t launch_scatter(const DevState& from, const DevState& to, int N, cons
                            int* err, cudaStream_t st);
 cudaError_t set_kernel_smem_limits(size_t sort_bytes);
 
+// The two state passes of a step (float4 records).
 cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 float* smax_out, unsigned long long* ncand,
                                 unsigned long long* nacc, double* acc, int* hist,
@@ -126,8 +144,6 @@ cudaError_t launch_unpack(const float4* P, float* y, float* vx, float* vy, float
                           cudaStream_t st);
 cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const float* vz,
                         float4* P, int N, cudaStream_t st);
-cudaError_t launch_init(float4* P, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
-                        int* err, cudaStream_t st);
 cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes);
 
 // Sets the message dsmc_last_error() returns on the calling thread.

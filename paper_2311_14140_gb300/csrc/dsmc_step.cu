@@ -38,7 +38,6 @@ namespace dsmc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kFlushEvery = 4;  // group samples per lane-accumulator flush
 
 // Scattering direction from one polar attempt (Marsaglia 1972): (a0, a1) uniform in
 // the unit disc gives n = (2 a0 sqrt(1-s), 2 a1 sqrt(1-s), 1 - 2 s), uniform on the
@@ -98,30 +97,25 @@ struct Moments {
   }
 };
 
-// Add a group's partial sums into this lane's column of the warp accumulators.
-__device__ __forceinline__ void add_to_lanes(float* lacc, const Moments& m, int lane) {
-#pragma unroll
-  for (int k = 0; k < kNMom; ++k) lacc[k * 32 + lane] += m.get(k);
-}
-
-// Warp sum of the lane accumulators, added (times 1/2: half a sample before and half
-// after the collisions) to the CTA's binary64 sums of one cell; accumulators cleared.
-__device__ __forceinline__ void flush_moments(float* lacc, double* cell_acc, int lane) {
+// Warp sum of a group's moment sums (pre- and post-collision), added (times 1/2: half a
+// sample before and half after the collisions) by lane 0 to the warp's binary64 sums of
+// the current cell.
+__device__ __forceinline__ void reduce_moments(const Moments& m, double* wsum, int lane) {
 #pragma unroll
   for (int k = 0; k < kNMom; ++k) {
-    float v = lacc[k * 32 + lane];
-    lacc[k * 32 + lane] = 0.0f;
+    float v = m.get(k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (lane == 0) atomicAdd(&cell_acc[k], 0.5 * (double)v);
+    if (lane == 0) wsum[k] += 0.5 * (double)v;
   }
 }
 
-// Per-cell results a warp gathered, added into the CTA's slots of that cell.
+// The warp's results for one cell, added into the CTA's slots of that cell (few
+// additions per cell: once per warp that worked on it).
 __device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
-                                           unsigned long long accn, unsigned* cgmax,
-                                           unsigned long long* ccand,
-                                           unsigned long long* caccn, int lane) {
+                                           unsigned long long accn, double* wsum, bool sample,
+                                           unsigned* cgmax, unsigned long long* ccand,
+                                           unsigned long long* caccn, double* cacc, int lane) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
@@ -131,7 +125,13 @@ __device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
     atomicMax(cgmax, __float_as_uint(gmax));  // gmax >= 0: bits order as values
     atomicAdd(ccand, cand);
     atomicAdd(caccn, accn);
+    if (sample)
+      for (int k = 0; k < kNMom; ++k) {
+        atomicAdd(&cacc[k], wsum[k]);
+        wsum[k] = 0.0;
+      }
   }
+  __syncwarp();
 }
 
 }  // namespace
@@ -139,13 +139,13 @@ __device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
 // Modes of the collision model: 0 hard spheres, 1 VHS with 0.5 < omega < 1,
 // 2 omega = 1 (sigma g independent of g).
 template <int kMode>
-__global__ void __launch_bounds__(kAWarps * 32, 2)
+__global__ void __launch_bounds__(kAWarps * 32, 3)
     k_collide_move(float4* __restrict__ P, const int* __restrict__ off,
                    const float* __restrict__ smax_in, float* __restrict__ smax_out,
                    unsigned long long* __restrict__ ncand, unsigned long long* __restrict__ nacc,
                    double* __restrict__ acc, int* __restrict__ hist, StepArgs a,
                    int* __restrict__ err) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int n_cells = a.n_cells;
   const int cps = a.cps;
   const int cap = a.cap;
@@ -161,28 +161,21 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   unsigned char* wmem = smem + L.warps + (size_t)wib * L.per_warp;
-  float* sx = reinterpret_cast<float*>(wmem);
-  float* sy = sx + cap;
-  float* sz = sy + cap;
-  float* spos = sz + cap;
-  int* own = reinterpret_cast<int*>(spos + cap);
-  float* lacc = reinterpret_cast<float*>(own + cap);  // kNMom x 32
+  float4* rec = reinterpret_cast<float4*>(wmem + L.w_rec);  // (y, vx, vy, vz) per particle
+  int* own = reinterpret_cast<int*>(wmem + L.w_own);
+  double* wsum = reinterpret_cast<double*>(wmem + L.w_sum);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wmem + L.w_bar);
 
   const int span = blockIdx.x;
   const int c0 = span * cps;
   const int c1 = min(c0 + cps, n_cells);
-  const unsigned lt = (1u << lane) - 1u;
   for (int i = threadIdx.x; i < n_cells; i += blockDim.x) h[i] = 0;
 
   if (a.count_only) {  // sort into cells: count the cells of the span's slots
     __syncthreads();
     const int b0 = off[c0], b1 = off[c1];
-    for (int base = b0 + wib * 32; base < b1; base += blockDim.x) {
-      const int p = base + lane;
-      const int cell = (p < b1) ? cell_of(P[p].x, n_cells, a.ncf) : -1;
-      const unsigned peers = __match_any_sync(kFull, cell);
-      if (cell >= 0 && (peers & lt) == 0) atomicAdd(&h[cell], __popc(peers));
-    }
+    for (int p = b0 + threadIdx.x; p < b1; p += blockDim.x)
+      atomicAdd(&h[cell_of(P[p].x, n_cells, a.ncf)], 1);
     __syncthreads();
     int* row = hist + (size_t)span * n_cells;
     for (int i = threadIdx.x; i < n_cells; i += blockDim.x) row[i] = h[i];
@@ -204,15 +197,19 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
     gfirst[c1 - c0] = q;
     *next_group = 0;
   }
-  for (int k = 0; k < kNMom; ++k) lacc[k * 32 + lane] = 0.0f;
+  if (lane == 0) {
+    for (int k = 0; k < kNMom; ++k) wsum[k] = 0.0;
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
   __syncthreads();
   const int n_groups = gfirst[c1 - c0];
 
-  bool bad_bounce = false, sphere_fail = false, cand_fail = false;
+  bool bad_bounce = false, sphere_fail = false, cand_fail = false, timeout = false;
+  uint32_t parity = 0;
   int cur = -1;  // local cell the warp is gathering results for
   float gmax = 0.0f;
   unsigned long long lcand = 0, laccn = 0;
-  int pending = 0;  // group samples in the lane accumulators
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(next_group, 1);
@@ -220,17 +217,6 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
     if (q >= n_groups) break;
     int lc = 0;
     while (gfirst[lc + 1] <= q) ++lc;
-    if (lc != cur) {  // results so far belong to another cell
-      if (cur >= 0) {
-        if (a.sample && pending > 0) flush_moments(lacc, cacc + (size_t)cur * kNMom, lane);
-        flush_cell(gmax, lcand, laccn, &cgmax[cur], &ccand[cur], &caccn[cur], lane);
-      }
-      cur = lc;
-      gmax = 0.0f;
-      lcand = 0;
-      laccn = 0;
-      pending = 0;
-    }
     const int c = c0 + lc;
     const int gi = q - gfirst[lc];
     const int start = off[c];
@@ -238,26 +224,42 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
     const int ng = gfirst[lc + 1] - gfirst[lc];
     const int gs = start + gi * G;
     const int gn = (gi == ng - 1) ? nc - gi * G : G;
-    const float smax = smax_in[c];
 
-    // 1. Stage the group; moments before the collisions.
-    {
-      Moments m;
-      m.zero();
-      for (int i = lane; i < gn; i += 32) {
-        const float4 r = P[gs + i];
-        spos[i] = r.x;
-        sx[i] = r.y;
-        sy[i] = r.z;
-        sz[i] = r.w;
-        own[i] = INT_MAX;
-        if (a.sample) m.add(r.y, r.z, r.w);
-      }
-      if (a.sample) add_to_lanes(lacc, m, lane);
-    }
+    // 1. Bulk copy of the group's records into shared memory (one lane issues it).
+    fence_proxy_async_smem();  // earlier generic accesses to rec before the async write
     __syncwarp();
+    if (lane == 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)gn * 16u);
+      bulk_load(rec, P + gs, (uint32_t)gn * 16u, bar);
+    }
+    if (lc != cur) {  // results so far belong to another cell
+      if (cur >= 0)
+        flush_cell(gmax, lcand, laccn, wsum, a.sample != 0, &cgmax[cur], &ccand[cur],
+                   &caccn[cur], cacc + (size_t)cur * kNMom, lane);
+      cur = lc;
+      gmax = 0.0f;
+      lcand = 0;
+      laccn = 0;
+    }
+    const float smax = smax_in[c];
+    for (int i = lane; i < gn; i += 32) own[i] = INT_MAX;
+    if (!mbar_wait(bar, parity)) {
+      timeout = true;
+      mbar_wait(bar, parity);  // give the copy one more bounded chance to land
+      break;
+    }
+    parity ^= 1u;
 
-    // 2. NTC candidates of the group.
+    // 2. Moments before the collisions.
+    Moments m;
+    m.zero();
+    if (a.sample)
+      for (int i = lane; i < gn; i += 32) {
+        const float4 r = rec[i];
+        m.add(r.y, r.z, r.w);
+      }
+
+    // 3. NTC candidates of the group.
     if (a.collide && gn >= 2) {
       const uint32_t c3 = (kStreamColl << 24) | ((uint32_t)gi << 4);
       const float t1 = fmul((float)(gn - 1), (float)nc);
@@ -314,24 +316,19 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
             own[j] = INT_MAX;
           }
           if (ready) {
-            const float xi = sx[i], yi = sy[i], zi = sz[i];
-            const float xj = sx[j], yj = sy[j], zj = sz[j];
-            const float gx = fsub(xi, xj), gy = fsub(yi, yj), gz = fsub(zi, zj);
+            const float4 ri = rec[i], rj = rec[j];
+            const float gx = fsub(ri.y, rj.y), gy = fsub(ri.z, rj.z), gz = fsub(ri.w, rj.w);
             const float g = fsqrt(fadd(fadd(fmul(gx, gx), fmul(gy, gy)), fmul(gz, gz)));
             gmax = fmaxf(gmax, g);
             if (g > thr) {
               if (have_dir) {
                 const float hg = fmul(0.5f, g);
-                const float cx = fmul(fadd(xi, xj), 0.5f);
-                const float cy = fmul(fadd(yi, yj), 0.5f);
-                const float cz = fmul(fadd(zi, zj), 0.5f);
+                const float cx = fmul(fadd(ri.y, rj.y), 0.5f);
+                const float cy = fmul(fadd(ri.z, rj.z), 0.5f);
+                const float cz = fmul(fadd(ri.w, rj.w), 0.5f);
                 const float dx = fmul(hg, nx), dy = fmul(hg, ny), dz = fmul(hg, nz);
-                sx[i] = fadd(cx, dx);
-                sy[i] = fadd(cy, dy);
-                sz[i] = fadd(cz, dz);
-                sx[j] = fsub(cx, dx);
-                sy[j] = fsub(cy, dy);
-                sz[j] = fsub(cz, dz);
+                rec[i] = make_float4(ri.x, fadd(cx, dx), fadd(cy, dy), fadd(cz, dz));
+                rec[j] = make_float4(rj.x, fsub(cx, dx), fsub(cy, dy), fsub(cz, dz));
                 laccn += 1;
               } else {
                 sphere_fail = true;
@@ -345,44 +342,26 @@ __global__ void __launch_bounds__(kAWarps * 32, 2)
     }
     __syncwarp();
 
-    // 3. Moments after the collisions, free flight, store, count the new cell.
-    {
-      Moments m;
-      m.zero();
-      for (int b = 0; b < gn; b += 32) {
-        const int i = b + lane;
-        const bool act = i < gn;
-        int cell = -1;
-        if (act) {
-          const int p = gs + i;
-          float yy = spos[i], xx = sx[i], uy = sy[i], zz = sz[i];
-          if (a.sample) m.add(xx, uy, zz);
-          if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, a.step, (uint32_t)p)) bad_bounce = true;
-          P[p] = make_float4(yy, xx, uy, zz);
-          cell = cell_of(yy, n_cells, a.ncf);
-        }
-        const unsigned peers = __match_any_sync(kFull, cell);
-        if (act && (peers & lt) == 0) atomicAdd(&h[cell], __popc(peers));
-      }
-      if (a.sample) {
-        add_to_lanes(lacc, m, lane);
-        pending += 2;
-        if (pending >= 2 * kFlushEvery) {
-          __syncwarp();
-          flush_moments(lacc, cacc + (size_t)cur * kNMom, lane);
-          pending = 0;
-        }
-      }
+    // 4. Moments after the collisions, free flight, store, count the new cell.
+    for (int i = lane; i < gn; i += 32) {
+      const int p = gs + i;
+      const float4 r = rec[i];
+      float yy = r.x, xx = r.y, uy = r.z, zz = r.w;
+      if (a.sample) m.add(xx, uy, zz);
+      if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, a.step, (uint32_t)p)) bad_bounce = true;
+      P[p] = make_float4(yy, xx, uy, zz);
+      atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
     }
+    if (a.sample) reduce_moments(m, wsum, lane);
     __syncwarp();
   }
-  if (cur >= 0) {
-    if (a.sample && pending > 0) flush_moments(lacc, cacc + (size_t)cur * kNMom, lane);
-    flush_cell(gmax, lcand, laccn, &cgmax[cur], &ccand[cur], &caccn[cur], lane);
-  }
+  if (cur >= 0)
+    flush_cell(gmax, lcand, laccn, wsum, a.sample != 0, &cgmax[cur], &ccand[cur], &caccn[cur],
+               cacc + (size_t)cur * kNMom, lane);
   if (bad_bounce) atomicOr(err, kErrBounces);
   if (sphere_fail) atomicOr(err, kErrSphere);
   if (cand_fail && lane == 0) atomicOr(err, kErrCandidates);
+  if (timeout && lane == 0) atomicOr(err, kErrCopyTimeout);
   __syncthreads();
 
   int* row = hist + (size_t)span * n_cells;
