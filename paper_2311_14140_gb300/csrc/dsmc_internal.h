@@ -78,7 +78,7 @@ struct StepArgs {
 // Dynamic shared memory of one collide/move CTA (byte offsets).
 struct StepSmem {
   size_t hist, cell_acc, cell_cand, cell_accn, cell_gmax, cell_groups, warps, per_warp, total;
-  size_t w_rec, w_own, w_sum, w_bar;  // offsets inside one warp's area
+  size_t w_rec, w_own, w_bar;  // offsets inside one warp's area
 };
 
 __host__ __device__ inline size_t step_align(size_t o, size_t a) { return (o + a - 1) / a * a; }
@@ -99,14 +99,12 @@ __host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int c
   L.cell_groups = o;  // group prefix of the span's cells (cps + 1) and a counter
   o = step_align(o + ((size_t)cps + 2) * 4, 128);
   // per warp: the group's records (cap float4, written by a bulk copy), an owner word
-  // per particle, 13 binary64 moment sums of the current cell, and an mbarrier
+  // per particle (reused as the queue of wall hits), and an mbarrier
   size_t w = 0;
   L.w_rec = w;
   w += (size_t)cap * 16;
   L.w_own = w;
   w = step_align(w + (size_t)cap * 4, 8);
-  L.w_sum = w;
-  w += (size_t)kNMom * 8;
   L.w_bar = w;
   w += 8;
   L.per_warp = step_align(w, 128);

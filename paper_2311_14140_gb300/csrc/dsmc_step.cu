@@ -97,25 +97,45 @@ struct Moments {
   }
 };
 
-// Warp sum of a group's moment sums (pre- and post-collision), added (times 1/2: half a
-// sample before and half after the collisions) by lane 0 to the warp's binary64 sums of
-// the current cell.
-__device__ __forceinline__ void reduce_moments(const Moments& m, double* wsum, int lane) {
+// Warp sums of a group's 13 moment sums (pre- plus post-collision), by a transposing
+// butterfly: each exchange halves the values a lane carries, so 16 shuffles leave the
+// total of moment idx(lane) on lanes 2i and 2i+1.  Lanes with an even id then add that
+// total into their Kahan-compensated binary32 running sum (ks, kc) for the cell.
+__device__ __forceinline__ int moment_of_lane(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+__device__ __forceinline__ void reduce_moments(const Moments& m, float& ks, float& kc,
+                                               int lane) {
+  float v[16];
 #pragma unroll
-  for (int k = 0; k < kNMom; ++k) {
-    float v = m.get(k);
+  for (int k = 0; k < 16; ++k) v[k] = (k < kNMom) ? m.get(k) : 0.0f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if (lane == 0) wsum[k] += 0.5 * (double)v;
+  for (int half = 8, mask = 16; half >= 1; half >>= 1, mask >>= 1) {
+    const bool upper = (lane & mask) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float send = upper ? v[k] : v[k + half];
+      const float keep = upper ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(kFull, send, mask);
+    }
+  }
+  const float tot = v[0] + __shfl_xor_sync(kFull, v[0], 1);
+  if ((lane & 1) == 0 && moment_of_lane(lane) < kNMom) {
+    const float yk = fsub(tot, kc);
+    const float t = fadd(ks, yk);
+    kc = fsub(fsub(t, ks), yk);
+    ks = t;
   }
 }
 
-// The warp's results for one cell, added into the CTA's slots of that cell (few
-// additions per cell: once per warp that worked on it).
+// The warp's results for one cell, added into the CTA's slots of that cell (once per
+// warp that worked on the cell).
 __device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
-                                           unsigned long long accn, double* wsum, bool sample,
-                                           unsigned* cgmax, unsigned long long* ccand,
-                                           unsigned long long* caccn, double* cacc, int lane) {
+                                           unsigned long long accn, float& ks, float& kc,
+                                           bool sample, unsigned* cgmax,
+                                           unsigned long long* ccand, unsigned long long* caccn,
+                                           double* cacc, int lane) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
@@ -125,12 +145,11 @@ __device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
     atomicMax(cgmax, __float_as_uint(gmax));  // gmax >= 0: bits order as values
     atomicAdd(ccand, cand);
     atomicAdd(caccn, accn);
-    if (sample)
-      for (int k = 0; k < kNMom; ++k) {
-        atomicAdd(&cacc[k], wsum[k]);
-        wsum[k] = 0.0;
-      }
   }
+  if (sample && (lane & 1) == 0 && moment_of_lane(lane) < kNMom)
+    atomicAdd(&cacc[moment_of_lane(lane)], 0.5 * ((double)ks - (double)kc));
+  ks = 0.0f;
+  kc = 0.0f;
   __syncwarp();
 }
 
@@ -162,13 +181,13 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   const int wib = threadIdx.x >> 5;
   unsigned char* wmem = smem + L.warps + (size_t)wib * L.per_warp;
   float4* rec = reinterpret_cast<float4*>(wmem + L.w_rec);  // (y, vx, vy, vz) per particle
-  int* own = reinterpret_cast<int*>(wmem + L.w_own);
-  double* wsum = reinterpret_cast<double*>(wmem + L.w_sum);
+  int* own = reinterpret_cast<int*>(wmem + L.w_own);  // also the queue of wall hits
   uint64_t* bar = reinterpret_cast<uint64_t*>(wmem + L.w_bar);
 
   const int span = blockIdx.x;
   const int c0 = span * cps;
   const int c1 = min(c0 + cps, n_cells);
+  const unsigned lt = (1u << lane) - 1u;
   for (int i = threadIdx.x; i < n_cells; i += blockDim.x) h[i] = 0;
 
   if (a.count_only) {  // sort into cells: count the cells of the span's slots
@@ -198,7 +217,6 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     *next_group = 0;
   }
   if (lane == 0) {
-    for (int k = 0; k < kNMom; ++k) wsum[k] = 0.0;
     mbar_init(bar, 1);
     fence_mbar_init();
   }
@@ -210,6 +228,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   int cur = -1;  // local cell the warp is gathering results for
   float gmax = 0.0f;
   unsigned long long lcand = 0, laccn = 0;
+  float ks = 0.0f, kc = 0.0f;  // this lane's compensated moment sum of the cell
   for (;;) {
     int q = 0;
     if (lane == 0) q = atomicAdd(next_group, 1);
@@ -234,7 +253,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     }
     if (lc != cur) {  // results so far belong to another cell
       if (cur >= 0)
-        flush_cell(gmax, lcand, laccn, wsum, a.sample != 0, &cgmax[cur], &ccand[cur],
+        flush_cell(gmax, lcand, laccn, ks, kc, a.sample != 0, &cgmax[cur], &ccand[cur],
                    &caccn[cur], cacc + (size_t)cur * kNMom, lane);
       cur = lc;
       gmax = 0.0f;
@@ -343,21 +362,46 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     __syncwarp();
 
     // 4. Moments after the collisions, free flight, store, count the new cell.
-    for (int i = lane; i < gn; i += 32) {
-      const int p = gs + i;
-      const float4 r = rec[i];
-      float yy = r.x, xx = r.y, uy = r.z, zz = r.w;
-      if (a.sample) m.add(xx, uy, zz);
-      if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, a.step, (uint32_t)p)) bad_bounce = true;
-      P[p] = make_float4(yy, xx, uy, zz);
-      atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
+    //    A particle whose flight reaches a wall is queued and flown afterwards, all such
+    //    particles of the group together (the free flight is exactly the first leg of
+    //    the full flight, so the result is the same).
+    int n_wall = 0;
+    for (int b = 0; b < gn; b += 32) {
+      const int i = b + lane;
+      bool hits = false;
+      if (i < gn) {
+        const float4 r = rec[i];
+        if (a.sample) m.add(r.y, r.z, r.w);
+        const float ynew = fadd(r.x, fmul(r.z, a.dt));
+        hits = (ynew < 0.0f) || (ynew > 1.0f);
+        if (!hits) {
+          const float xx = fadd(r.y, fmul(a.F, a.dt));
+          P[gs + i] = make_float4(ynew, xx, r.z, r.w);
+          atomicAdd(&h[cell_of(ynew, n_cells, a.ncf)], 1);
+        }
+      }
+      const unsigned q = __ballot_sync(kFull, hits);
+      if (hits) own[n_wall + __popc(q & lt)] = i;
+      n_wall += __popc(q);
     }
-    if (a.sample) reduce_moments(m, wsum, lane);
+    __syncwarp();
+    for (int b = 0; b < n_wall; b += 32) {
+      if (b + lane < n_wall) {
+        const int i = own[b + lane];
+        const int p = gs + i;
+        const float4 r = rec[i];
+        float yy = r.x, xx = r.y, uy = r.z, zz = r.w;
+        if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, a.step, (uint32_t)p)) bad_bounce = true;
+        P[p] = make_float4(yy, xx, uy, zz);
+        atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
+      }
+    }
+    if (a.sample) reduce_moments(m, ks, kc, lane);
     __syncwarp();
   }
   if (cur >= 0)
-    flush_cell(gmax, lcand, laccn, wsum, a.sample != 0, &cgmax[cur], &ccand[cur], &caccn[cur],
-               cacc + (size_t)cur * kNMom, lane);
+    flush_cell(gmax, lcand, laccn, ks, kc, a.sample != 0, &cgmax[cur], &ccand[cur],
+               &caccn[cur], cacc + (size_t)cur * kNMom, lane);
   if (bad_bounce) atomicOr(err, kErrBounces);
   if (sphere_fail) atomicOr(err, kErrSphere);
   if (cand_fail && lane == 0) atomicOr(err, kErrCandidates);

@@ -3,12 +3,13 @@
 Deterministic mode: both sides draw the same Philox streams keyed on (step, slot,
 bounce) and (step, cell, group, candidate) and round every binary32 operation once,
 so particle state, cell offsets (the sort order), (sigma g)_max and collision
-counters must agree bit for bit.  The moment sums are binary64 on both sides but the
-CUDA path adds the products of a collision group in binary32 first (per lane, then a
-5-level shuffle tree over at most 767 particles: at most 24 + 5 = 29 roundings of
-relative size 2^-24 on partial sums bounded by the sum of |products|), so they must
-agree within 29 * 2^-24 * sum|product| < 2e-6 * sum|product|, with sum|product| from
-the oracle.
+counters must agree bit for bit.  The moment sums are binary64 in the oracle; the CUDA
+path adds a collision group's products in binary32 (per lane at most 24 terms: 12 before
+and 12 after the collisions, then 5 butterfly levels across the warp) and the group
+totals of a cell in compensated (Kahan) binary32 before one binary64 addition.  Each
+product thus passes through at most 24 + 5 + 2 = 31 roundings of relative size 2^-24
+on partial sums bounded by the sum of |products|, so the sums must agree within
+31 * 2^-24 * sum|product| < 2e-6 * sum|product|, with sum|product| from the oracle.
 
 Statistical mode: independent seeds on each side; time-averaged velocity, shear
 stress and heat flux agree within the combined standard errors.
