@@ -107,6 +107,7 @@ typedef struct dsmc_info {
   float coef;          /* n sigma_ref dt / (2 ppc): NTC candidate factor */
   float cvhs, vexp;    /* sigma g / sigma_ref = cvhs * g^vexp (HS: 1, 1) */
   float vinv;          /* 1 / vexp (0 when omega = 1) */
+  float lncv;          /* ln cvhs */
   float smax0;         /* initial (sigma g)_max / sigma_ref */
   size_t device_bytes; /* device memory the handle uses */
   int sort_warps;      /* partition of the stand-alone sort into cells */

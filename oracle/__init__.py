@@ -237,11 +237,11 @@ class OracleSim:
         return lib().or_error(self.h)
 
     def params(self):
-        f = np.zeros(7, np.float32)
+        f = np.zeros(8, np.float32)
         d = np.zeros(2, np.float64)
         lib().or_params(self.h, _ptr(f), _ptr(d))
         return {"dt": f[0], "F": f[1], "coef": f[2], "cvhs": f[3], "vexp": f[4],
-                "smax0": f[5], "vinv": f[6], "nsig": d[0], "dt_d": d[1]}
+                "smax0": f[5], "vinv": f[6], "lncv": f[7], "nsig": d[0], "dt_d": d[1]}
 
     def state(self):
         arrs = [np.empty(self.N, np.float32) for _ in range(4)]

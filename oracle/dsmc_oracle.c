@@ -280,7 +280,7 @@ typedef struct {
   /* derived */
   int N;
   double nsig, dt_d;
-  float dt, F, coef, cvhs, vexp, vinv, smax0, ncf;
+  float dt, F, coef, cvhs, vexp, vinv, lncv, smax0, ncf;
   /* state: sorted by cell */
   float *y, *vx, *vy, *vz;
   float *ty, *tvx, *tvy, *tvz; /* sort scratch */
@@ -419,16 +419,18 @@ static float sigma_g(const osim* s, float g) {
 /* NTC acceptance, sigma(g) g > u (sigma g)_max (probability sigma g / (sigma g)_max),
  * written as a threshold on the relative speed, g > thr:
  *   hard spheres:  thr = u (sigma g)_max;
- *   VHS, w < 1:    thr = (u (sigma g)_max / cvhs)^(1/(2-2w)), since sigma g grows
- *                  monotonically with g;
+ *   VHS, w < 1:    thr = (u (sigma g)_max / cvhs)^(1/(2-2w))
+ *                      = exp((ln(u (sigma g)_max) - ln cvhs) / (2-2w)),
+ *                  since sigma g grows monotonically with g (ln cvhs is a run
+ *                  constant, so no division per candidate);
  *   w = 1:         sigma g = cvhs for every g: thr = -1 (accept) when
  *                  u (sigma g)_max < cvhs, else +inf (reject). */
 static float accept_threshold(const osim* s, float u, float smax) {
   float us = u * smax;
   if (s->omega == 0.5) return us;
   if (s->omega == 1.0) return (us < s->cvhs) ? -1.0f : INFINITY;
-  float t = us / s->cvhs;
-  return or_exp(s->vinv * or_ln(t));
+  float t = or_ln(us) - s->lncv;
+  return or_exp(s->vinv * t);
 }
 
 /* Post-collision velocities of an accepted pair (isotropic scattering, which both
@@ -646,6 +648,7 @@ OR_EXPORT osim* or_create(double omega, double Kn, double F, int n_cells, int pp
   s->cvhs = (float)cv;
   s->vexp = (float)(2.0 - 2.0 * omega);
   s->vinv = (omega < 1.0) ? (float)(1.0 / (2.0 - 2.0 * omega)) : 0.0f;
+  s->lncv = (float)log(cv);
   s->smax0 = (float)(cv * pow(5.0, 2.0 - 2.0 * omega));
   s->ncf = (float)n_cells;
   size_t n = (size_t)s->N, nb = n ? n : 1;
@@ -689,11 +692,11 @@ OR_EXPORT int or_n_particles(const osim* s) { return s->N; }
 OR_EXPORT long long or_step_count(const osim* s) { return s->step; }
 OR_EXPORT int or_error(const osim* s) { return s->err; }
 
-/* dt, F, coef, cvhs, vexp, smax0, vinv as the binary32 values the step uses, and
- * nsig, dt in binary64. */
+/* dt, F, coef, cvhs, vexp, smax0, vinv, lncv as the binary32 values the step uses,
+ * and nsig, dt in binary64. */
 OR_EXPORT void or_params(const osim* s, float* f6, double* d2) {
   f6[0] = s->dt; f6[1] = s->F; f6[2] = s->coef; f6[3] = s->cvhs; f6[4] = s->vexp;
-  f6[5] = s->smax0; f6[6] = s->vinv;
+  f6[5] = s->smax0; f6[6] = s->vinv; f6[7] = s->lncv;
   d2[0] = s->nsig; d2[1] = s->dt_d;
 }
 

@@ -123,7 +123,7 @@ Layout make_layout(int n_cells, int ppc) {
 // use them.
 struct Params {
   double nsig, dt;
-  float dt_f, F_f, coef, cvhs, vexp, vinv, smax0;
+  float dt_f, F_f, coef, cvhs, vexp, vinv, lncv, smax0;
 };
 
 // n sigma_ref H from Kn through mu0 v0 / (P0 H) = 2 Kn / sqrt(pi) (Eq. 7) and the
@@ -159,6 +159,7 @@ bool derive_params(double omega, double Kn, double F, int ppc, const dsmc_option
   p->cvhs = (float)cv;
   p->vexp = (float)(2.0 - 2.0 * omega);
   p->vinv = (omega < 1.0) ? (float)(1.0 / (2.0 - 2.0 * omega)) : 0.0f;
+  p->lncv = (float)std::log(cv);
   p->smax0 = (float)(cv * std::pow(5.0, 2.0 - 2.0 * omega));
   return std::isfinite(dt) && dt > 0.0;
 }
@@ -271,10 +272,31 @@ StepArgs step_args(const dsmc_sim* h, bool count_only) {
   const bool sampling = h->step >= h->opt.sample_start;
   const bool collide = h->opt.collisions != 0 && h->p.nsig > 0.0;
   const int mode = (h->omega == 0.5) ? 0 : (h->omega == 1.0 ? 2 : 1);
-  return StepArgs{h->n_cells, h->L.cps, G + G / 2 - 1, G, h->ncf, h->p.dt_f, h->p.F_f,
-                  h->p.coef, h->p.cvhs, h->p.vexp, h->p.vinv, h->k0(), h->k1(),
-                  (uint32_t)h->step, (sampling && !count_only) ? 1 : 0,
-                  (collide && !count_only) ? 1 : 0, mode, count_only ? 1 : 0};
+  StepArgs a{};
+  a.n_cells = h->n_cells;
+  a.cps = h->L.cps;
+  a.cap = G + G / 2 - 1;
+  a.G = G;
+  a.ncf = h->ncf;
+  a.dt = h->p.dt_f;
+  a.F = h->p.F_f;
+  a.coef = h->p.coef;
+  a.cvhs = h->p.cvhs;
+  a.vexp = h->p.vexp;
+  a.vinv = h->p.vinv;
+  a.lncv = h->p.lncv;
+  a.k0 = h->k0();
+  a.k1 = h->k1();
+  for (int r = 0; r < 10; ++r) {
+    a.keys.k0[r] = a.k0 + (uint32_t)r * 0x9E3779B9u;
+    a.keys.k1[r] = a.k1 + (uint32_t)r * 0xBB67AE85u;
+  }
+  a.step = (uint32_t)h->step;
+  a.sample = (sampling && !count_only) ? 1 : 0;
+  a.collide = (collide && !count_only) ? 1 : 0;
+  a.mode = mode;
+  a.count_only = count_only ? 1 : 0;
+  return a;
 }
 
 // Sort into cells without moving (creation, state load).  off[ocur] must describe
@@ -676,6 +698,7 @@ dsmc_status dsmc_get_info(dsmc_handle h, dsmc_info* info) {
   info->cvhs = h->p.cvhs;
   info->vexp = h->p.vexp;
   info->vinv = h->p.vinv;
+  info->lncv = h->p.lncv;
   info->smax0 = h->p.smax0;
   info->device_bytes = h->L.total;
   info->sort_warps = h->L.plan.n_warps;

@@ -50,6 +50,24 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
   return U4{c0, c1, c2, c3};
 }
 
+// The same generator with the round keys precomputed (kernel arguments), so a round
+// is two wide multiplies and two three-input XORs.
+__device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        const PhiloxKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c0 = n0;
+    c1 = (uint32_t)p1;
+    c2 = n2;
+    c3 = (uint32_t)p0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
 // Uniform in (0,1) from the top 23 bits: (m + 1/2) 2^-23, exact in binary32.
 __device__ __forceinline__ float u01(uint32_t x) {
   return fmul(fadd((float)(x >> 9), 0.5f), 0x1p-23f);

@@ -57,6 +57,11 @@ struct MoveArgs {
   int do_move;
 };
 
+// The round keys of Philox4x32-10 for one key: round r uses (k0 + r W0, k1 + r W1).
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
 // Arguments of the collide/move pass.
 struct StepArgs {
   int n_cells;
@@ -67,7 +72,9 @@ struct StepArgs {
   float dt, F;
   float coef;              // n sigma_ref dt / (2 ppc)
   float cvhs, vexp, vinv;  // VHS factor, exponent 2 - 2 omega and its inverse
+  float lncv;              // ln cvhs
   uint32_t k0, k1;         // Philox key (seed)
+  PhiloxKeys keys;         // the ten round keys of that key
   uint32_t step;
   int sample;
   int collide;

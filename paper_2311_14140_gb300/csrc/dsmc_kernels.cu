@@ -97,23 +97,34 @@ __global__ void k_move_count(float* __restrict__ y, float* __restrict__ vx,
 }
 
 // For each cell c: hist[w][c] <- sum_{w' < w} hist[w'][c]; count[c] <- total.
-// Block (32, 8): x = cell within a chunk of 32, y = one of 8 contiguous row segments.
-__global__ void k_scan_hist(int* __restrict__ hist, int n_warps, int n_cells,
-                            int* __restrict__ count) {
-  __shared__ int seg_tot[8][33];
+// Block (32, 32): x = cell within a chunk of 32 cells, y = one of 32 contiguous row
+// segments; each pass keeps eight independent loads per thread in flight.
+constexpr int kScanSegs = 32;
+__global__ void __launch_bounds__(32 * kScanSegs)
+    k_scan_hist(int* __restrict__ hist, int n_warps, int n_cells, int* __restrict__ count) {
+  __shared__ int seg_tot[kScanSegs][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int c = blockIdx.x * 32 + tx;
-  const int seg = (n_warps + 7) / 8;
-  const int r0 = ty * seg;
+  const int seg = (n_warps + kScanSegs - 1) / kScanSegs;
+  const int r0 = min(n_warps, ty * seg);
   const int r1 = min(n_warps, r0 + seg);
   int s = 0;
-  if (c < n_cells)
-    for (int r = r0; r < r1; ++r) s += hist[(size_t)r * n_cells + c];
+  if (c < n_cells) {
+    int r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      int v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = hist[(size_t)(r + u) * n_cells + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; r < r1; ++r) s += hist[(size_t)r * n_cells + c];
+  }
   seg_tot[ty][tx] = s;
   __syncthreads();
   if (ty == 0) {
     int run = 0;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kScanSegs; ++k) {
       const int v = seg_tot[k][tx];
       seg_tot[k][tx] = run;
       run += v;
@@ -123,7 +134,18 @@ __global__ void k_scan_hist(int* __restrict__ hist, int n_warps, int n_cells,
   __syncthreads();
   if (c < n_cells) {
     int run = seg_tot[ty][tx];
-    for (int r = r0; r < r1; ++r) {
+    int r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      int v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = hist[(size_t)(r + u) * n_cells + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        hist[(size_t)(r + u) * n_cells + c] = run;
+        run += v[u];
+      }
+    }
+    for (; r < r1; ++r) {
       const size_t i = (size_t)r * n_cells + c;
       const int v = hist[i];
       hist[i] = run;
@@ -232,7 +254,7 @@ cudaError_t launch_move_count(const DevState& s, int N, const SortPlan& sp, int 
 
 cudaError_t launch_scan_hist(int* hist, int n_warps, int n_cells, int* count, cudaStream_t st) {
   const int blocks = (n_cells + 31) / 32;
-  k_scan_hist<<<blocks, dim3(32, 8), 0, st>>>(hist, n_warps, n_cells, count);
+  k_scan_hist<<<blocks, dim3(32, kScanSegs), 0, st>>>(hist, n_warps, n_cells, count);
   return cudaGetLastError();
 }
 

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
       const float fl = floorf(mf);
       const float frac = fsub(mf, fl);
       uint32_t M = (uint32_t)fl;
-      const U4 r = philox(0xffffffffu, (uint32_t)c, a.step, c3, a.k0, a.k1);
+      const U4 r = philox_rk(0xffffffffu, (uint32_t)c, a.step, c3, a.keys);
       if (u01(r.x) < frac) M += 1;
       if (!(mf <= kMaxCandidates)) {
         M = 0;
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
         float thr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
         bool have_dir = false;
         if (pend) {
-          const U4 w = philox(k, (uint32_t)c, a.step, c3, a.k0, a.k1);
+          const U4 w = philox_rk(k, (uint32_t)c, a.step, c3, a.keys);
           i = (int)__umulhi(w.x, (uint32_t)gn);
           j = (int)__umulhi(w.y, (uint32_t)(gn - 1));
           j += (j >= i) ? 1 : 0;
@@ -308,17 +308,17 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
           if (kMode == 0)
             thr = us;
           else if (kMode == 1)
-            thr = exp32(fmul(a.vinv, ln32(fdiv(us, a.cvhs))));
+            thr = exp32(fmul(a.vinv, fsub(ln32(us), a.lncv)));
           else
             thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
-          const U4 d = philox(k, (uint32_t)c, a.step, c3 | 1u, a.k0, a.k1);
+          const U4 d = philox_rk(k, (uint32_t)c, a.step, c3 | 1u, a.keys);
           have_dir = sphere(d.x, d.y, nx, ny, nz) || sphere(d.z, d.w, nx, ny, nz);
         }
         if (__any_sync(kFull, pend && !have_dir)) {
           // Rare: both attempts of the first draw fell outside the disc.
           for (int at = 2; at < kNormalAttempts && pend && !have_dir; at += 2) {
-            const U4 d = philox(k, (uint32_t)c, a.step, c3 | (1u + (uint32_t)(at >> 1)),
-                                a.k0, a.k1);
+            const U4 d = philox_rk(k, (uint32_t)c, a.step, c3 | (1u + (uint32_t)(at >> 1)),
+                                   a.keys);
             have_dir = sphere(d.x, d.y, nx, ny, nz) || sphere(d.z, d.w, nx, ny, nz);
           }
         }
@@ -422,14 +422,57 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   }
 }
 
-// One warp per span: stable scatter of the span's records into the other buffer.  Each
-// lane keeps kUnroll records in flight before any of them is placed.
+// One warp per span: stable scatter of the span's records into the other buffer.  Slots
+// are taken 256 at a time (8 per lane); the loads of the next 256 are issued before the
+// current ones are placed, so each lane keeps 8 to 16 records in flight.
+namespace {
+
+constexpr int kScatterUnroll = 8;
+
+__device__ __forceinline__ void load_batch(float4 (&r)[kScatterUnroll],
+                                           const float4* __restrict__ P, int base, int b1,
+                                           int lane) {
+#pragma unroll
+  for (int u = 0; u < kScatterUnroll; ++u) {
+    const int p = base + u * 32 + lane;
+    if (p < b1) r[u] = P[p];
+  }
+}
+
+__device__ __forceinline__ bool place_batch(const float4 (&r)[kScatterUnroll],
+                                            float4* __restrict__ P2, int* run, int base, int b1,
+                                            int n_cells, float ncf, int N, int lane,
+                                            unsigned lt) {
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < kScatterUnroll; ++u) {
+    const int p = base + u * 32 + lane;
+    const bool act = p < b1;
+    const int cell = act ? cell_of(r[u].x, n_cells, ncf) : -1;
+    const unsigned peers = __match_any_sync(kFull, cell);
+    const int first = act ? run[cell] : 0;
+    __syncwarp();
+    if (act && (peers & lt) == 0) run[cell] = first + __popc(peers);
+    __syncwarp();
+    if (act) {
+      const int d = first + __popc(peers & lt);
+      if (d >= 0 && d < N)
+        P2[d] = r[u];
+      else
+        bad = true;
+    }
+  }
+  return bad;
+}
+
+}  // namespace
+
 __global__ void __launch_bounds__(kBWarpsMax * 32)
     k_scatter_spans(const float4* __restrict__ P, float4* __restrict__ P2,
                     const int* __restrict__ off_cur, const int* __restrict__ off_new,
                     const int* __restrict__ hist, int n_cells, int cps, int n_spans, float ncf,
                     int N, int* __restrict__ err) {
-  constexpr int kUnroll = 16;
+  constexpr int kBatch = 32 * kScatterUnroll;
   extern __shared__ int sh_run[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -445,31 +488,14 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   const int b1 = off_cur[c1];
   const unsigned lt = (1u << lane) - 1u;
   bool bad = false;
-  for (int base = b0; base < b1; base += 32 * kUnroll) {
-    float4 rec[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int p = base + u * 32 + lane;
-      if (p < b1) rec[u] = P[p];
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int p = base + u * 32 + lane;
-      const bool act = p < b1;
-      const int cell = act ? cell_of(rec[u].x, n_cells, ncf) : -1;
-      const unsigned peers = __match_any_sync(kFull, cell);
-      const int first = act ? run[cell] : 0;
-      __syncwarp();
-      if (act && (peers & lt) == 0) run[cell] = first + __popc(peers);
-      __syncwarp();
-      if (act) {
-        const int d = first + __popc(peers & lt);
-        if (d >= 0 && d < N)
-          P2[d] = rec[u];
-        else
-          bad = true;
-      }
-    }
+  float4 ra[kScatterUnroll], rb[kScatterUnroll];
+  load_batch(ra, P, b0, b1, lane);
+  for (int base = b0; base < b1; base += 2 * kBatch) {
+    load_batch(rb, P, base + kBatch, b1, lane);
+    bad |= place_batch(ra, P2, run, base, b1, n_cells, ncf, N, lane, lt);
+    if (base + kBatch >= b1) break;
+    load_batch(ra, P, base + 2 * kBatch, b1, lane);
+    bad |= place_batch(rb, P2, run, base + kBatch, b1, n_cells, ncf, N, lane, lt);
   }
   if (bad) atomicOr(err, kErrSort);
 }

@@ -49,7 +49,7 @@ class Info(ctypes.Structure):
                 ("omega", ctypes.c_double), ("body_force", ctypes.c_double),
                 ("nsigma", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dt_f", ctypes.c_float), ("F_f", ctypes.c_float), ("coef", ctypes.c_float),
-                ("cvhs", ctypes.c_float), ("vexp", ctypes.c_float), ("vinv", ctypes.c_float),
+                ("cvhs", ctypes.c_float), ("vexp", ctypes.c_float), ("vinv", ctypes.c_float), ("lncv", ctypes.c_float),
                 ("smax0", ctypes.c_float), ("device_bytes", ctypes.c_size_t),
                 ("sort_warps", ctypes.c_int), ("sort_span", ctypes.c_int),
                 ("cells_per_span", ctypes.c_int), ("n_spans", ctypes.c_int)]

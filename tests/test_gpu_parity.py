@@ -78,7 +78,7 @@ def test_parameters_match_oracle(omega, Kn, ppc, dt, dtf):
         o, g = make_pair(omega=omega, Kn=Kn, n_cells=1, ppc=ppc, dt=dt, dt_factor=dtf)
         po, pg = o.params(), g.info()
     for ko, kg in (("dt", "dt_f"), ("F", "F_f"), ("coef", "coef"), ("cvhs", "cvhs"),
-                   ("vexp", "vexp"), ("smax0", "smax0")):
+                   ("vexp", "vexp"), ("smax0", "smax0"), ("vinv", "vinv"), ("lncv", "lncv")):
         assert np.float32(po[ko]).view(np.uint32) == np.float32(pg[kg]).view(np.uint32), ko
     assert po["nsig"] == pg["nsigma"] and po["dt_d"] == pg["dt"]
 
