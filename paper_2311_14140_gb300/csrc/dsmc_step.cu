@@ -39,18 +39,20 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Scattering direction from one polar attempt (Marsaglia 1972): (a0, a1) uniform in
-// the unit disc gives n = (2 a0 sqrt(1-s), 2 a1 sqrt(1-s), 1 - 2 s), uniform on the
-// sphere.
-__device__ __forceinline__ bool sphere(uint32_t w0, uint32_t w1, float& nx, float& ny,
-                                       float& nz) {
-  const float a0 = s11(w0);
-  const float a1 = s11(w1);
-  const float sq = fadd(fmul(a0, a0), fmul(a1, a1));
-  if (sq >= 1.0f) return false;
+// Scattering direction from the first of two polar attempts (Marsaglia 1972) that
+// falls inside the unit disc: (a0, a1) gives n = (2 a0 sqrt(1-s), 2 a1 sqrt(1-s),
+// 1 - 2 s), uniform on the sphere.  Returns false when both fall outside.
+__device__ __forceinline__ bool sphere2(const U4& w, float& nx, float& ny, float& nz) {
+  const float a0 = s11(w.x), a1 = s11(w.y);
+  const float b0 = s11(w.z), b1 = s11(w.w);
+  const float sa = fadd(fmul(a0, a0), fmul(a1, a1));
+  const float sb = fadd(fmul(b0, b0), fmul(b1, b1));
+  const bool first = sa < 1.0f;
+  if (!first && !(sb < 1.0f)) return false;
+  const float c0 = first ? a0 : b0, c1 = first ? a1 : b1, sq = first ? sa : sb;
   const float q = fmul(2.0f, fsqrt(fsub(1.0f, sq)));
-  nx = fmul(a0, q);
-  ny = fmul(a1, q);
+  nx = fmul(c0, q);
+  ny = fmul(c1, q);
   nz = fsub(1.0f, fmul(2.0f, sq));
   return true;
 }
@@ -181,7 +183,10 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   const int wib = threadIdx.x >> 5;
   unsigned char* wmem = smem + L.warps + (size_t)wib * L.per_warp;
   float4* rec = reinterpret_cast<float4*>(wmem + L.w_rec);  // (y, vx, vy, vz) per particle
-  int* own = reinterpret_cast<int*>(wmem + L.w_own);  // also the queue of wall hits
+  // Per particle of the staged group: during a batch of candidates, the lanes whose
+  // candidates touch it (bit mask); zero between batches.  Also the queue of wall hits
+  // (then restored to zero).
+  unsigned* touch = reinterpret_cast<unsigned*>(wmem + L.w_own);
   uint64_t* bar = reinterpret_cast<uint64_t*>(wmem + L.w_bar);
 
   const int span = blockIdx.x;
@@ -216,6 +221,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     gfirst[c1 - c0] = q;
     *next_group = 0;
   }
+  for (int i = lane; i < cap; i += 32) touch[i] = 0u;
   if (lane == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -261,7 +267,6 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
       laccn = 0;
     }
     const float smax = smax_in[c];
-    for (int i = lane; i < gn; i += 32) own[i] = INT_MAX;
     if (!mbar_wait(bar, parity)) {
       timeout = true;
       mbar_wait(bar, parity);  // give the copy one more bounded chance to land
@@ -312,28 +317,34 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
           else
             thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
           const U4 d = philox_rk(k, (uint32_t)c, a.step, c3 | 1u, a.keys);
-          have_dir = sphere(d.x, d.y, nx, ny, nz) || sphere(d.z, d.w, nx, ny, nz);
+          have_dir = sphere2(d, nx, ny, nz);
         }
         if (__any_sync(kFull, pend && !have_dir)) {
-          // Rare: both attempts of the first draw fell outside the disc.
+          // Both attempts of the first draw fell outside the disc (4.6 % of candidates).
           for (int at = 2; at < kNormalAttempts && pend && !have_dir; at += 2) {
             const U4 d = philox_rk(k, (uint32_t)c, a.step, c3 | (1u + (uint32_t)(at >> 1)),
                                    a.keys);
-            have_dir = sphere(d.x, d.y, nx, ny, nz) || sphere(d.z, d.w, nx, ny, nz);
+            have_dir = sphere2(d, nx, ny, nz);
           }
         }
-        while (__any_sync(kFull, pend)) {
-          if (pend) {
-            atomicMin(&own[i], lane);
-            atomicMin(&own[j], lane);
-          }
-          __syncwarp();
-          const bool ready = pend && own[i] == lane && own[j] == lane;
-          __syncwarp();
-          if (pend) {
-            own[i] = INT_MAX;
-            own[j] = INT_MAX;
-          }
+        // Earlier candidates of the batch that share a particle with this one: the
+        // candidate may be applied once none of them is pending any more, which gives
+        // exactly the result of applying the candidates in order.
+        if (pend) {
+          atomicOr(&touch[i], 1u << lane);
+          atomicOr(&touch[j], 1u << lane);
+        }
+        __syncwarp();
+        const unsigned before = pend ? ((touch[i] | touch[j]) & lt) : 0u;
+        __syncwarp();
+        if (pend) {
+          touch[i] = 0u;
+          touch[j] = 0u;
+        }
+        for (;;) {
+          const unsigned waiting = __ballot_sync(kFull, pend);
+          if (waiting == 0u) break;
+          const bool ready = pend && (before & waiting) == 0u;
           if (ready) {
             const float4 ri = rec[i], rj = rec[j];
             const float gx = fsub(ri.y, rj.y), gy = fsub(ri.z, rj.z), gz = fsub(ri.w, rj.w);
@@ -381,13 +392,13 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
         }
       }
       const unsigned q = __ballot_sync(kFull, hits);
-      if (hits) own[n_wall + __popc(q & lt)] = i;
+      if (hits) touch[n_wall + __popc(q & lt)] = (unsigned)i;
       n_wall += __popc(q);
     }
     __syncwarp();
     for (int b = 0; b < n_wall; b += 32) {
       if (b + lane < n_wall) {
-        const int i = own[b + lane];
+        const int i = (int)touch[b + lane];
         const int p = gs + i;
         const float4 r = rec[i];
         float yy = r.x, xx = r.y, uy = r.z, zz = r.w;
@@ -396,6 +407,8 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
         atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
       }
     }
+    __syncwarp();
+    for (int i = lane; i < n_wall; i += 32) touch[i] = 0u;
     if (a.sample) reduce_moments(m, ks, kc, lane);
     __syncwarp();
   }
