@@ -235,10 +235,13 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   float gmax = 0.0f;
   unsigned long long lcand = 0, laccn = 0;
   float ks = 0.0f, kc = 0.0f;  // this lane's compensated moment sum of the cell
+  // Groups are handed out by a counter; each warp reserves its next group one step
+  // ahead and prefetches its records into L2 while it works on the current one.
+  int q_next = 0;
+  if (lane == 0) q_next = atomicAdd(next_group, 1);
+  q_next = __shfl_sync(kFull, q_next, 0);
   for (;;) {
-    int q = 0;
-    if (lane == 0) q = atomicAdd(next_group, 1);
-    q = __shfl_sync(kFull, q, 0);
+    const int q = q_next;
     if (q >= n_groups) break;
     int lc = 0;
     while (gfirst[lc + 1] <= q) ++lc;
@@ -249,6 +252,18 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     const int ng = gfirst[lc + 1] - gfirst[lc];
     const int gs = start + gi * G;
     const int gn = (gi == ng - 1) ? nc - gi * G : G;
+    if (lane == 0) q_next = atomicAdd(next_group, 1);
+    q_next = __shfl_sync(kFull, q_next, 0);
+    if (q_next < n_groups && lane == 0) {
+      int ln = lc;
+      while (gfirst[ln + 1] <= q_next) ++ln;
+      const int cn = c0 + ln;
+      const int gin = q_next - gfirst[ln];
+      const int ncn = off[cn + 1] - off[cn];
+      const int ngn = gfirst[ln + 1] - gfirst[ln];
+      const int gnn = (gin == ngn - 1) ? ncn - gin * G : G;
+      bulk_prefetch_l2(P + off[cn] + gin * G, (uint32_t)gnn * 16u);
+    }
 
     // 1. Bulk copy of the group's records into shared memory (one lane issues it).
     fence_proxy_async_smem();  // earlier generic accesses to rec before the async write
