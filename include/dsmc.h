@@ -89,11 +89,20 @@ typedef struct dsmc_options {
   int collisions;         /* 0 turns collisions off; default 1 */
   int profile;            /* 1: time every kernel launch with CUDA events (then
                              dsmc_step synchronises at its end); default 0 */
+  int span_particles;     /* particles per span (CTA) of the step passes at the
+                             initial density: 0 keeps the partition in use (2048 at
+                             creation, or what dsmc_autotune chose), else 1024..2^24.
+                             Only the work split changes: results are identical for
+                             every value; default 0 */
+  int graph;              /* 1: dsmc_step replays the launches of 16 steps as one
+                             CUDA graph (captured on first use; needs a stream other
+                             than the legacy default; off while profiling); results
+                             are identical; default 0 */
   void* stream;           /* cudaStream_t for all work; default NULL */
 } dsmc_options;
 
-/* What the handle computes with: the binary32 values are exactly those the kernels
- * use. */
+/* What one instance of a handle computes with: the binary32 values are exactly those
+ * the kernels use. */
 typedef struct dsmc_info {
   long long n_particles;
   int n_cells;
@@ -109,12 +118,25 @@ typedef struct dsmc_info {
   float vinv;          /* 1 / vexp (0 when omega = 1) */
   float lncv;          /* ln cvhs */
   float smax0;         /* initial (sigma g)_max / sigma_ref */
-  size_t device_bytes; /* device memory the handle uses */
-  int sort_warps;      /* partition of the stand-alone sort into cells */
-  int sort_span;       /* particles per partition of that sort */
-  int cells_per_span;  /* cells per span of the step's two state passes */
-  int n_spans;         /* spans (CTAs of the collide/move pass) */
+  size_t device_bytes; /* device memory the whole handle uses */
+  int n_instances;     /* instances in the handle */
+  int span_particles;  /* particles per span of the partition in use */
+  int cells_per_span;  /* this instance's cells per span of the step passes */
+  int n_spans;         /* this instance's spans (CTAs of the collide/move pass) */
+  int total_spans;     /* spans of all instances */
+  int first_slot;      /* the instance's first particle slot in the handle */
 } dsmc_info;
+
+/* One member of a batch: the arguments of dsmc_create. */
+typedef struct dsmc_instance {
+  dsmc_gas gas;
+  double Kn;
+  double wall_T;
+  double body_force;
+  int n_cells;
+  int ppc;
+  uint64_t seed;
+} dsmc_instance;
 
 typedef struct dsmc_sim* dsmc_handle;
 
@@ -188,6 +210,62 @@ DSMC_API dsmc_status dsmc_load_state(dsmc_handle h, const float* y, const float*
                             long long step);
 
 DSMC_API dsmc_status dsmc_get_info(dsmc_handle h, dsmc_info* info);
+
+/* Batches: many independent runs advanced by the same launches.
+ *
+ * The paper's method trains its surrogate on many micro-simulations at different
+ * (Kn, force) points (Sec. 2.3-2.4); a batch runs them together so that small runs
+ * fill the GPU.  Instance i of a batch evolves bit for bit as dsmc_create_in with
+ * instances[i] and the same options would: its random numbers are keyed on its own
+ * seed, step, cells and slots.  Instances may differ in gas, Kn, wall_T, force,
+ * n_cells and ppc; options (dt_factor or dt, group size, sampling start, stream) are
+ * shared.  Particle slots, cells and sort matrices are concatenated in one device
+ * workspace (dsmc_batch_workspace_bytes); every step is the same four launches as
+ * for one run, over the spans of all instances.  The functions without `_of` act on
+ * instance 0, dsmc_step and dsmc_reset_samples on all instances. */
+
+/* Device bytes dsmc_create_batch needs (0 for invalid sizes). */
+DSMC_API size_t dsmc_batch_workspace_bytes(const dsmc_instance* instances, int n_instances);
+
+/* Create n_instances (1..65535) runs in one handle; each instance is validated as by
+ * dsmc_create (messages name the failing instance), and all particles, each instance
+ * padded to a multiple of 64, must total <= 2^31 - 2^24.  workspace as for
+ * dsmc_create_in (NULL: the library allocates).  Synchronises. */
+DSMC_API dsmc_status dsmc_create_batch(const dsmc_instance* instances, int n_instances,
+                                       const dsmc_options* opt, void* workspace,
+                                       size_t workspace_bytes, dsmc_handle* out);
+
+/* Number of instances (0 for NULL). */
+DSMC_API int dsmc_batch_size(dsmc_handle h);
+
+/* Per-instance forms of the functions above, instance index 0 <= i < batch size. */
+DSMC_API dsmc_status dsmc_sample_moments_of(dsmc_handle h, int i, double* out,
+                                            long long* n_samples);
+DSMC_API dsmc_status dsmc_reset_samples_of(dsmc_handle h, int i);
+DSMC_API dsmc_status dsmc_copy_state_of(dsmc_handle h, int i, float* y, float* vx, float* vy,
+                                        float* vz);
+/* offset[] is relative to the instance's first slot, as for a run of its own. */
+DSMC_API dsmc_status dsmc_copy_cells_of(dsmc_handle h, int i, int* offset, float* smax,
+                                        unsigned long long* ncand, unsigned long long* nacc);
+DSMC_API dsmc_status dsmc_load_state_of(dsmc_handle h, int i, const float* y, const float* vx,
+                                        const float* vy, const float* vz, const float* smax,
+                                        long long step);
+DSMC_API dsmc_status dsmc_get_info_of(dsmc_handle h, int i, dsmc_info* info);
+
+/* The moment sums of all instances in one copy: out holds sum(n_cells_i) x DSMC_NMOM
+ * binary64 values, instance after instance; n_samples (NULL or batch-size entries)
+ * gets each instance's sampled steps.  Synchronises. */
+DSMC_API dsmc_status dsmc_sample_moments_all(dsmc_handle h, double* out, long long* n_samples);
+
+/* Tuner of the step partition.  For span sizes 1024, 2048, ... particles (those whose
+ * shared memory fits, skipping sizes that give the same partition) it runs one
+ * untimed and steps_per_trial timed steps, keeps the fastest, and stores it in the
+ * handle's options (span_particles).  The trial steps are real steps of the run: they
+ * advance every instance, and since the partition does not change results the run is
+ * the same as without tuning.  *best_span_particles and *best_ms_per_step (either may
+ * be NULL) get the choice and its time per step.  Synchronises. */
+DSMC_API dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_particles,
+                                   double* best_ms_per_step);
 
 /* Kernel timing (options.profile = 1).  For kernel id k < dsmc_kernel_count():
  * total milliseconds and launches since the last dsmc_reset_kernel_times. */

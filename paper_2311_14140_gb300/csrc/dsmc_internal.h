@@ -62,12 +62,25 @@ struct PhiloxKeys {
   uint32_t k0[10], k1[10];
 };
 
-// Arguments of the collide/move pass.
-struct StepArgs {
+// One simulation instance as the step kernels see it.  A run holds one or more
+// instances; their particles, cells, spans and sort matrices are concatenated, and the
+// fields below place instance i in those arrays.  Random numbers are keyed on the
+// instance's own seed, step, local cell and local slot, so an instance evolves the
+// same alone and in a batch.
+struct InstParams {
+  // placement in the concatenated arrays
   int n_cells;
-  int cps;   // cells per span (one CTA each)
-  int cap;   // largest group: G + G/2 - 1
+  int cell_base;   // first index of the instance in per-cell arrays
+  int off_base;    // first index in the cell-offset arrays (n_cells + 1 entries)
+  int span_base;   // first global span
+  int n_spans;
+  int cps;         // cells per span (one collide/move CTA each)
+  int part_base;   // first global slot of the instance's particles
+  int n_part;
+  long long hist_base;  // first entry of the instance's sort matrix (n_spans x n_cells)
+  // method parameters, binary32 as the kernels use them
   int G;
+  int cap;  // largest group: G + G/2 - 1
   float ncf;
   float dt, F;
   float coef;              // n sigma_ref dt / (2 ppc)
@@ -75,11 +88,10 @@ struct StepArgs {
   float lncv;              // ln cvhs
   uint32_t k0, k1;         // Philox key (seed)
   PhiloxKeys keys;         // the ten round keys of that key
-  uint32_t step;
-  int sample;
+  long long step0;         // the instance's step k runs at global step step0 + k
+  long long sample_start;  // instance steps >= sample_start are sampled
   int collide;
-  int mode;        // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
-  int count_only;  // only count the cells of the span's slots (sort into cells)
+  int mode;  // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
 };
 
 // Dynamic shared memory of one collide/move CTA (byte offsets).
@@ -123,6 +135,7 @@ __host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int c
 
 cudaError_t launch_init(float4* P, int N, int ppc, float ncf, uint32_t k0, uint32_t k1,
                         int* err, cudaStream_t st);
+int scatter_spans_warps(int n_cells);
 
 // Sort into cells over fixed spans of slots, four separate arrays (the
 // allocation-free sort); the prefix kernels are also used by every step.
@@ -136,15 +149,35 @@ cudaError_t launch_scatter(const DevState& from, const DevState& to, int N, cons
                            int* err, cudaStream_t st);
 cudaError_t set_kernel_smem_limits(size_t sort_bytes);
 
-// The two state passes of a step (float4 records).
+// The two state passes of a step (float4 records).  With one instance the
+// parameters travel as a kernel argument; with several, kernels read the run's
+// instance table in device memory, finding a span's instance through span_inst.
+struct StepLaunch {
+  int n_inst;
+  const InstParams* tab;  // device, n_inst entries (batched launches)
+  const int* span_inst;   // device, one entry per global span (batched launches)
+  int n_spans_total;
+  int max_cells;         // largest n_cells of the instances
+  int max_cps;
+  int max_cap;
+  long long gstep;       // global step number
+  long long* gstep_dev;  // non-NULL (graph replay): read the step number here instead;
+                         // the cell-offset kernel advances it at the end of the step
+  int count_only;
+};
 cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 float* smax_out, unsigned long long* ncand,
                                 unsigned long long* nacc, double* acc, int* hist,
-                                const StepArgs& a, int n_spans, int* err, cudaStream_t st);
-int scatter_spans_warps(int n_cells);
+                                const InstParams& one, const StepLaunch& L, int* err,
+                                cudaStream_t st);
 cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur,
-                                 const int* off_new, const int* hist, int n_cells, int cps,
-                                 int n_spans, float ncf, int N, int* err, cudaStream_t st);
+                                 const int* off_new, const int* hist, const InstParams& one,
+                                 const StepLaunch& L, int* err, cudaStream_t st);
+cudaError_t launch_scan_spans(int* hist, int* count, const InstParams& one, const StepLaunch& L,
+                              cudaStream_t st);
+cudaError_t launch_offsets_cells(const int* count, int* off_new, const InstParams& one,
+                                 const StepLaunch& L, cudaStream_t st);
+cudaError_t launch_set_counter(long long* counter, long long value, cudaStream_t st);
 cudaError_t launch_unpack(const float4* P, float* y, float* vx, float* vy, float* vz, int N,
                           cudaStream_t st);
 cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const float* vz,

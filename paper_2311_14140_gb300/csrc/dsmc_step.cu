@@ -157,16 +157,62 @@ __device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
 
 }  // namespace
 
-// Modes of the collision model: 0 hard spheres, 1 VHS with 0.5 < omega < 1,
-// 2 omega = 1 (sigma g independent of g).
-template <int kMode>
+// The parameters of the instance a span belongs to: the kernel argument for a
+// single-instance run, else the entry of the run's instance table.
+template <bool kBatch>
+__device__ __forceinline__ const InstParams& instance_of(const InstParams& one,
+                                                         const StepLaunch& SL, int span) {
+  if constexpr (kBatch)
+    return SL.tab[SL.span_inst[span]];
+  else
+    return one;
+}
+
+// Copies the CTA's instance entry into shared memory (one read of the table per CTA,
+// then broadcast reads); returns the copy, or the kernel argument for one instance.
+template <bool kBatch>
+__device__ __forceinline__ const InstParams& stage_instance(const InstParams& one,
+                                                            const StepLaunch& SL, int span,
+                                                            InstParams* sh) {
+  if constexpr (kBatch) {
+    static_assert(sizeof(InstParams) % 4 == 0, "InstParams is copied as words");
+    const int* src = reinterpret_cast<const int*>(&SL.tab[SL.span_inst[span]]);
+    int* dst = reinterpret_cast<int*>(sh);
+    for (int i = threadIdx.x; i < (int)(sizeof(InstParams) / 4); i += blockDim.x)
+      dst[i] = src[i];
+    __syncthreads();
+    return *sh;
+  } else {
+    return one;
+  }
+}
+
+// Collision models (a.mode): 0 hard spheres, 1 VHS with 0.5 < omega < 1, 2 omega = 1
+// (sigma g independent of g).
+template <bool kBatch>
 __global__ void __launch_bounds__(kAWarps * 32, 3)
-    k_collide_move(float4* __restrict__ P, const int* __restrict__ off,
-                   const float* __restrict__ smax_in, float* __restrict__ smax_out,
-                   unsigned long long* __restrict__ ncand, unsigned long long* __restrict__ nacc,
-                   double* __restrict__ acc, int* __restrict__ hist, StepArgs a,
+    k_collide_move(float4* __restrict__ P, const int* __restrict__ off_all,
+                   const float* __restrict__ smax_in_all, float* __restrict__ smax_out_all,
+                   unsigned long long* __restrict__ ncand_all,
+                   unsigned long long* __restrict__ nacc_all, double* __restrict__ acc_all,
+                   int* __restrict__ hist, const InstParams one, const StepLaunch SL,
                    int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ InstParams sh_inst;
+  const InstParams& a = stage_instance<kBatch>(one, SL, blockIdx.x, &sh_inst);
+  const int* __restrict__ off = off_all + a.off_base;
+  const float* __restrict__ smax_in = smax_in_all + a.cell_base;
+  float* __restrict__ smax_out = smax_out_all + a.cell_base;
+  unsigned long long* __restrict__ ncand = ncand_all + a.cell_base;
+  unsigned long long* __restrict__ nacc = nacc_all + a.cell_base;
+  double* __restrict__ acc = acc_all + (size_t)a.cell_base * kNMom;
+  // the instance's step number
+  const long long istep = (SL.gstep_dev ? *SL.gstep_dev : SL.gstep) - a.step0;
+  const uint32_t step = (uint32_t)istep;
+  const bool count_only = SL.count_only != 0;
+  const bool sample = !count_only && istep >= a.sample_start;
+  const bool collide = !count_only && a.collide != 0;
+  const int mode = a.mode;
   const int n_cells = a.n_cells;
   const int cps = a.cps;
   const int cap = a.cap;
@@ -189,19 +235,19 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   unsigned* touch = reinterpret_cast<unsigned*>(wmem + L.w_own);
   uint64_t* bar = reinterpret_cast<uint64_t*>(wmem + L.w_bar);
 
-  const int span = blockIdx.x;
+  const int span = blockIdx.x - a.span_base;  // the instance's span
   const int c0 = span * cps;
   const int c1 = min(c0 + cps, n_cells);
   const unsigned lt = (1u << lane) - 1u;
+  int* row = hist + a.hist_base + (size_t)span * n_cells;
   for (int i = threadIdx.x; i < n_cells; i += blockDim.x) h[i] = 0;
 
-  if (a.count_only) {  // sort into cells: count the cells of the span's slots
+  if (count_only) {  // sort into cells: count the cells of the span's slots
     __syncthreads();
     const int b0 = off[c0], b1 = off[c1];
     for (int p = b0 + threadIdx.x; p < b1; p += blockDim.x)
       atomicAdd(&h[cell_of(P[p].x, n_cells, a.ncf)], 1);
     __syncthreads();
-    int* row = hist + (size_t)span * n_cells;
     for (int i = threadIdx.x; i < n_cells; i += blockDim.x) row[i] = h[i];
     return;
   }
@@ -274,7 +320,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     }
     if (lc != cur) {  // results so far belong to another cell
       if (cur >= 0)
-        flush_cell(gmax, lcand, laccn, ks, kc, a.sample != 0, &cgmax[cur], &ccand[cur],
+        flush_cell(gmax, lcand, laccn, ks, kc, sample, &cgmax[cur], &ccand[cur],
                    &caccn[cur], cacc + (size_t)cur * kNMom, lane);
       cur = lc;
       gmax = 0.0f;
@@ -292,21 +338,21 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     // 2. Moments before the collisions.
     Moments m;
     m.zero();
-    if (a.sample)
+    if (sample)
       for (int i = lane; i < gn; i += 32) {
         const float4 r = rec[i];
         m.add(r.y, r.z, r.w);
       }
 
     // 3. NTC candidates of the group.
-    if (a.collide && gn >= 2) {
+    if (collide && gn >= 2) {
       const uint32_t c3 = (kStreamColl << 24) | ((uint32_t)gi << 4);
       const float t1 = fmul((float)(gn - 1), (float)nc);
       const float mf = fmul(fmul(t1, a.coef), smax);
       const float fl = floorf(mf);
       const float frac = fsub(mf, fl);
       uint32_t M = (uint32_t)fl;
-      const U4 r = philox_rk(0xffffffffu, (uint32_t)c, a.step, c3, a.keys);
+      const U4 r = philox_rk(0xffffffffu, (uint32_t)c, step, c3, a.keys);
       if (u01(r.x) < frac) M += 1;
       if (!(mf <= kMaxCandidates)) {
         M = 0;
@@ -320,24 +366,24 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
         float thr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
         bool have_dir = false;
         if (pend) {
-          const U4 w = philox_rk(k, (uint32_t)c, a.step, c3, a.keys);
+          const U4 w = philox_rk(k, (uint32_t)c, step, c3, a.keys);
           i = (int)__umulhi(w.x, (uint32_t)gn);
           j = (int)__umulhi(w.y, (uint32_t)(gn - 1));
           j += (j >= i) ? 1 : 0;
           const float us = fmul(u01(w.z), smax);
-          if (kMode == 0)
+          if (mode == 0)
             thr = us;
-          else if (kMode == 1)
+          else if (mode == 1)
             thr = exp32(fmul(a.vinv, fsub(ln32(us), a.lncv)));
           else
             thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
-          const U4 d = philox_rk(k, (uint32_t)c, a.step, c3 | 1u, a.keys);
+          const U4 d = philox_rk(k, (uint32_t)c, step, c3 | 1u, a.keys);
           have_dir = sphere2(d, nx, ny, nz);
         }
         if (__any_sync(kFull, pend && !have_dir)) {
           // Both attempts of the first draw fell outside the disc (4.6 % of candidates).
           for (int at = 2; at < kNormalAttempts && pend && !have_dir; at += 2) {
-            const U4 d = philox_rk(k, (uint32_t)c, a.step, c3 | (1u + (uint32_t)(at >> 1)),
+            const U4 d = philox_rk(k, (uint32_t)c, step, c3 | (1u + (uint32_t)(at >> 1)),
                                    a.keys);
             have_dir = sphere2(d, nx, ny, nz);
           }
@@ -397,7 +443,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
       bool hits = false;
       if (i < gn) {
         const float4 r = rec[i];
-        if (a.sample) m.add(r.y, r.z, r.w);
+        if (sample) m.add(r.y, r.z, r.w);
         const float ynew = fadd(r.x, fmul(r.z, a.dt));
         hits = (ynew < 0.0f) || (ynew > 1.0f);
         if (!hits) {
@@ -417,18 +463,19 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
         const int p = gs + i;
         const float4 r = rec[i];
         float yy = r.x, xx = r.y, uy = r.z, zz = r.w;
-        if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, a.step, (uint32_t)p)) bad_bounce = true;
+        if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, step, (uint32_t)(p - a.part_base)))
+          bad_bounce = true;
         P[p] = make_float4(yy, xx, uy, zz);
         atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
       }
     }
     __syncwarp();
     for (int i = lane; i < n_wall; i += 32) touch[i] = 0u;
-    if (a.sample) reduce_moments(m, ks, kc, lane);
+    if (sample) reduce_moments(m, ks, kc, lane);
     __syncwarp();
   }
   if (cur >= 0)
-    flush_cell(gmax, lcand, laccn, ks, kc, a.sample != 0, &cgmax[cur], &ccand[cur],
+    flush_cell(gmax, lcand, laccn, ks, kc, sample, &cgmax[cur], &ccand[cur],
                &caccn[cur], cacc + (size_t)cur * kNMom, lane);
   if (bad_bounce) atomicOr(err, kErrBounces);
   if (sphere_fail) atomicOr(err, kErrSphere);
@@ -436,16 +483,15 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   if (timeout && lane == 0) atomicOr(err, kErrCopyTimeout);
   __syncthreads();
 
-  int* row = hist + (size_t)span * n_cells;
   for (int i = threadIdx.x; i < n_cells; i += blockDim.x) row[i] = h[i];
   for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     const int lc = c - c0;
     const float gm = __uint_as_float(cgmax[lc]);
-    const float sg = (kMode == 0) ? gm : fmul(a.cvhs, pow32(gm, a.vexp));
+    const float sg = (mode == 0) ? gm : fmul(a.cvhs, pow32(gm, a.vexp));
     smax_out[c] = fmaxf(smax_in[c], sg);
     ncand[c] += ccand[lc];
     nacc[c] += caccn[lc];
-    if (a.sample)
+    if (sample)
       for (int k = 0; k < kNMom; ++k) acc[(size_t)c * kNMom + k] += cacc[lc * kNMom + k];
   }
 }
@@ -469,7 +515,7 @@ __device__ __forceinline__ void load_batch(float4 (&r)[kScatterUnroll],
 
 __device__ __forceinline__ bool place_batch(const float4 (&r)[kScatterUnroll],
                                             float4* __restrict__ P2, int* run, int base, int b1,
-                                            int n_cells, float ncf, int N, int lane,
+                                            int n_cells, float ncf, int lo, int hi, int lane,
                                             unsigned lt) {
   bool bad = false;
 #pragma unroll
@@ -484,7 +530,7 @@ __device__ __forceinline__ bool place_batch(const float4 (&r)[kScatterUnroll],
     __syncwarp();
     if (act) {
       const int d = first + __popc(peers & lt);
-      if (d >= 0 && d < N)
+      if (d >= lo && d < hi)
         P2[d] = r[u];
       else
         bad = true;
@@ -495,38 +541,147 @@ __device__ __forceinline__ bool place_batch(const float4 (&r)[kScatterUnroll],
 
 }  // namespace
 
+template <bool kBatch>
 __global__ void __launch_bounds__(kBWarpsMax * 32)
     k_scatter_spans(const float4* __restrict__ P, float4* __restrict__ P2,
-                    const int* __restrict__ off_cur, const int* __restrict__ off_new,
-                    const int* __restrict__ hist, int n_cells, int cps, int n_spans, float ncf,
-                    int N, int* __restrict__ err) {
-  constexpr int kBatch = 32 * kScatterUnroll;
+                    const int* __restrict__ off_cur_all, const int* __restrict__ off_new_all,
+                    const int* __restrict__ hist, const InstParams one, const StepLaunch SL,
+                    int* __restrict__ err) {
+  constexpr int kBatch2 = 32 * kScatterUnroll;
   extern __shared__ int sh_run[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int span = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (span >= n_spans) return;
-  int* run = sh_run + (size_t)wib * n_cells;
-  const int* row = hist + (size_t)span * n_cells;
+  const int gspan = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (gspan >= SL.n_spans_total) return;
+  const InstParams& a = instance_of<kBatch>(one, SL, gspan);
+  const int n_cells = a.n_cells;
+  const int span = gspan - a.span_base;
+  const int* __restrict__ off_cur = off_cur_all + a.off_base;
+  const int* __restrict__ off_new = off_new_all + a.off_base;
+  int* run = sh_run + (size_t)wib * SL.max_cells;
+  const int* row = hist + a.hist_base + (size_t)span * n_cells;
   for (int c = lane; c < n_cells; c += 32) run[c] = off_new[c] + row[c];
   __syncwarp();
-  const int c0 = span * cps;
-  const int c1 = min(c0 + cps, n_cells);
+  const int c0 = span * a.cps;
+  const int c1 = min(c0 + a.cps, n_cells);
   const int b0 = off_cur[c0];
   const int b1 = off_cur[c1];
+  const int lo = a.part_base, hi = a.part_base + a.n_part;  // the instance's slots
   const unsigned lt = (1u << lane) - 1u;
   bool bad = false;
   float4 ra[kScatterUnroll], rb[kScatterUnroll];
   load_batch(ra, P, b0, b1, lane);
-  for (int base = b0; base < b1; base += 2 * kBatch) {
-    load_batch(rb, P, base + kBatch, b1, lane);
-    bad |= place_batch(ra, P2, run, base, b1, n_cells, ncf, N, lane, lt);
-    if (base + kBatch >= b1) break;
-    load_batch(ra, P, base + 2 * kBatch, b1, lane);
-    bad |= place_batch(rb, P2, run, base + kBatch, b1, n_cells, ncf, N, lane, lt);
+  for (int base = b0; base < b1; base += 2 * kBatch2) {
+    load_batch(rb, P, base + kBatch2, b1, lane);
+    bad |= place_batch(ra, P2, run, base, b1, n_cells, a.ncf, lo, hi, lane, lt);
+    if (base + kBatch2 >= b1) break;
+    load_batch(ra, P, base + 2 * kBatch2, b1, lane);
+    bad |= place_batch(rb, P2, run, base + kBatch2, b1, n_cells, a.ncf, lo, hi, lane, lt);
   }
   if (bad) atomicOr(err, kErrSort);
 }
+
+// Per instance and cell c: row r of the sort matrix <- sum over rows r' < r (the spans
+// before), count[c] <- total.  Block (32, 32): x = cell within a chunk of 32, y = one of
+// 32 contiguous row segments; grid (cell chunks, instances).
+template <bool kBatch>
+__global__ void __launch_bounds__(1024)
+    k_scan_spans(int* __restrict__ hist, int* __restrict__ count_all, const InstParams one,
+                 const StepLaunch SL) {
+  __shared__ int seg_tot[32][33];
+  const InstParams& a = kBatch ? SL.tab[blockIdx.y] : one;
+  const int n_cells = a.n_cells;
+  if ((int)blockIdx.x * 32 >= n_cells) return;
+  const int n_rows = a.n_spans;
+  int* __restrict__ m = hist + a.hist_base;
+  int* __restrict__ count = count_all + a.cell_base;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int c = blockIdx.x * 32 + tx;
+  const int seg = (n_rows + 31) / 32;
+  const int r0 = min(n_rows, ty * seg);
+  const int r1 = min(n_rows, r0 + seg);
+  int s = 0;
+  if (c < n_cells) {
+    int r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      int v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = m[(size_t)(r + u) * n_cells + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; r < r1; ++r) s += m[(size_t)r * n_cells + c];
+  }
+  seg_tot[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0) {
+    int run = 0;
+    for (int k = 0; k < 32; ++k) {
+      const int v = seg_tot[k][tx];
+      seg_tot[k][tx] = run;
+      run += v;
+    }
+    if (c < n_cells) count[c] = run;
+  }
+  __syncthreads();
+  if (c < n_cells) {
+    int run = seg_tot[ty][tx];
+    int r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      int v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = m[(size_t)(r + u) * n_cells + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        m[(size_t)(r + u) * n_cells + c] = run;
+        run += v[u];
+      }
+    }
+    for (; r < r1; ++r) {
+      const size_t i = (size_t)r * n_cells + c;
+      const int v = m[i];
+      m[i] = run;
+      run += v;
+    }
+  }
+}
+
+// Per instance (one CTA each): off_new[c] = first global slot of cell c,
+// off_new[n_cells] = end of the instance's slots.
+template <bool kBatch>
+__global__ void __launch_bounds__(1024)
+    k_offsets_cells(const int* __restrict__ count_all, int* __restrict__ off_new_all,
+                    const InstParams one, const StepLaunch SL) {
+  __shared__ int part[1024];
+  const InstParams& a = kBatch ? SL.tab[blockIdx.x] : one;
+  const int n_cells = a.n_cells;
+  const int* __restrict__ count = count_all + a.cell_base;
+  int* __restrict__ offset = off_new_all + a.off_base;
+  const int t = threadIdx.x;
+  const int per = (n_cells + 1023) / 1024;
+  const int cb = t * per;
+  const int ce = min(n_cells, cb + per);
+  int s = 0;
+  for (int c = cb; c < ce; ++c) s += count[c];
+  part[t] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {  // inclusive Hillis-Steele scan
+    const int v = t >= d ? part[t - d] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = a.part_base + (t > 0 ? part[t - 1] : 0);
+  for (int c = cb; c < ce; ++c) {
+    offset[c] = run;
+    run += count[c];
+  }
+  if (t == 1023) offset[n_cells] = a.part_base + part[1023];
+  // Graph replay: the step's collide/move pass has finished reading the step number.
+  if (SL.gstep_dev != nullptr && blockIdx.x == 0 && t == 0) *SL.gstep_dev += 1;
+}
+
+__global__ void k_set_counter(long long* counter, long long value) { *counter = value; }
 
 // Records <-> four arrays (y, vx, vy, vz), for the state accessors.
 __global__ void k_unpack(const float4* __restrict__ P, float* __restrict__ y,
@@ -557,22 +712,16 @@ __global__ void k_pack(const float* __restrict__ y, const float* __restrict__ vx
 cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 float* smax_out, unsigned long long* ncand,
                                 unsigned long long* nacc, double* acc, int* hist,
-                                const StepArgs& a, int n_spans, int* err, cudaStream_t st) {
-  const StepSmem L = step_smem_layout(a.n_cells, a.cps, a.cap);
+                                const InstParams& one, const StepLaunch& L, int* err,
+                                cudaStream_t st) {
+  const StepSmem S = step_smem_layout(L.max_cells, L.max_cps, L.max_cap);
   const dim3 block(kAWarps * 32);
-  switch (a.mode) {
-    case 0:
-      k_collide_move<0><<<n_spans, block, L.total, st>>>(P, off, smax_in, smax_out, ncand, nacc,
-                                                          acc, hist, a, err);
-      break;
-    case 1:
-      k_collide_move<1><<<n_spans, block, L.total, st>>>(P, off, smax_in, smax_out, ncand, nacc,
-                                                          acc, hist, a, err);
-      break;
-    default:
-      k_collide_move<2><<<n_spans, block, L.total, st>>>(P, off, smax_in, smax_out, ncand, nacc,
-                                                          acc, hist, a, err);
-  }
+  if (L.n_inst == 1)
+    k_collide_move<false><<<L.n_spans_total, block, S.total, st>>>(
+        P, off, smax_in, smax_out, ncand, nacc, acc, hist, one, L, err);
+  else
+    k_collide_move<true><<<L.n_spans_total, block, S.total, st>>>(
+        P, off, smax_in, smax_out, ncand, nacc, acc, hist, one, L, err);
   return cudaGetLastError();
 }
 
@@ -583,13 +732,41 @@ int scatter_spans_warps(int n_cells) {
 }
 
 cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur,
-                                 const int* off_new, const int* hist, int n_cells, int cps,
-                                 int n_spans, float ncf, int N, int* err, cudaStream_t st) {
-  const int wpb = scatter_spans_warps(n_cells);
-  const size_t smem = (size_t)wpb * n_cells * sizeof(int);
-  const int blocks = (n_spans + wpb - 1) / wpb;
-  k_scatter_spans<<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, n_cells, cps,
-                                                 n_spans, ncf, N, err);
+                                 const int* off_new, const int* hist, const InstParams& one,
+                                 const StepLaunch& L, int* err, cudaStream_t st) {
+  const int wpb = scatter_spans_warps(L.max_cells);
+  const size_t smem = (size_t)wpb * L.max_cells * sizeof(int);
+  const int blocks = (L.n_spans_total + wpb - 1) / wpb;
+  if (L.n_inst == 1)
+    k_scatter_spans<false><<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, one, L,
+                                                          err);
+  else
+    k_scatter_spans<true><<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, one, L,
+                                                         err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_spans(int* hist, int* count, const InstParams& one, const StepLaunch& L,
+                              cudaStream_t st) {
+  const dim3 grid((L.max_cells + 31) / 32, L.n_inst);
+  if (L.n_inst == 1)
+    k_scan_spans<false><<<grid, dim3(32, 32), 0, st>>>(hist, count, one, L);
+  else
+    k_scan_spans<true><<<grid, dim3(32, 32), 0, st>>>(hist, count, one, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_offsets_cells(const int* count, int* off_new, const InstParams& one,
+                                 const StepLaunch& L, cudaStream_t st) {
+  if (L.n_inst == 1)
+    k_offsets_cells<false><<<1, 1024, 0, st>>>(count, off_new, one, L);
+  else
+    k_offsets_cells<true><<<L.n_inst, 1024, 0, st>>>(count, off_new, one, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_counter(long long* counter, long long value, cudaStream_t st) {
+  k_set_counter<<<1, 1, 0, st>>>(counter, value);
   return cudaGetLastError();
 }
 
@@ -609,16 +786,16 @@ cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const 
 
 cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes) {
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_collide_move<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_collide_move<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)a_bytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_collide_move<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_collide_move<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)a_bytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_collide_move<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)a_bytes);
+  e = cudaFuncSetAttribute(k_scatter_spans<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)b_bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_scatter_spans, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_scatter_spans<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)b_bytes);
 }
 

@@ -39,6 +39,7 @@ class Options(ctypes.Structure):
     _fields_ = [("dt_factor", ctypes.c_double), ("dt", ctypes.c_double),
                 ("sample_start", ctypes.c_longlong), ("group_size", ctypes.c_int),
                 ("collisions", ctypes.c_int), ("profile", ctypes.c_int),
+                ("span_particles", ctypes.c_int), ("graph", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -51,8 +52,15 @@ class Info(ctypes.Structure):
                 ("dt_f", ctypes.c_float), ("F_f", ctypes.c_float), ("coef", ctypes.c_float),
                 ("cvhs", ctypes.c_float), ("vexp", ctypes.c_float), ("vinv", ctypes.c_float), ("lncv", ctypes.c_float),
                 ("smax0", ctypes.c_float), ("device_bytes", ctypes.c_size_t),
-                ("sort_warps", ctypes.c_int), ("sort_span", ctypes.c_int),
-                ("cells_per_span", ctypes.c_int), ("n_spans", ctypes.c_int)]
+                ("n_instances", ctypes.c_int), ("span_particles", ctypes.c_int),
+                ("cells_per_span", ctypes.c_int), ("n_spans", ctypes.c_int),
+                ("total_spans", ctypes.c_int), ("first_slot", ctypes.c_int)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("gas", Gas), ("Kn", ctypes.c_double), ("wall_T", ctypes.c_double),
+                ("body_force", ctypes.c_double), ("n_cells", ctypes.c_int),
+                ("ppc", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 _lib = None
@@ -88,6 +96,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsmc_load_state": (st, [H, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p,
                                  c.c_void_p, c.c_longlong]),
         "dsmc_get_info": (st, [H, c.POINTER(Info)]),
+        "dsmc_batch_workspace_bytes": (c.c_size_t, [c.POINTER(Instance), c.c_int]),
+        "dsmc_create_batch": (st, [c.POINTER(Instance), c.c_int, c.POINTER(Options), c.c_void_p,
+                                   c.c_size_t, c.POINTER(H)]),
+        "dsmc_batch_size": (c.c_int, [H]),
+        "dsmc_sample_moments_of": (st, [H, c.c_int, c.c_void_p, c.POINTER(c.c_longlong)]),
+        "dsmc_sample_moments_all": (st, [H, c.c_void_p, c.c_void_p]),
+        "dsmc_reset_samples_of": (st, [H, c.c_int]),
+        "dsmc_copy_state_of": (st, [H, c.c_int, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "dsmc_copy_cells_of": (st, [H, c.c_int, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "dsmc_load_state_of": (st, [H, c.c_int, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p,
+                                    c.c_void_p, c.c_longlong]),
+        "dsmc_get_info_of": (st, [H, c.c_int, c.POINTER(Info)]),
+        "dsmc_autotune": (st, [H, c.c_int, c.POINTER(c.c_int), c.POINTER(c.c_double)]),
+        "dsmc_sort_cells_static": (st, [c.c_void_p] * 9 + [c.c_int, c.c_int, c.c_void_p]),
         "dsmc_kernel_count": (c.c_int, []),
         "dsmc_kernel_name": (c.c_char_p, [c.c_int]),
         "dsmc_kernel_times": (st, [H, c.c_void_p, c.c_void_p]),
@@ -142,6 +164,7 @@ class Dsmc:
                  body_force: float = 0.0, seed: int = 0, wall_T: float = 273.0,
                  dt_factor: float = 0.2, dt: float = 0.0, sample_start: int = 0,
                  group_size: int = 256, collisions: bool = True, profile: bool = False,
+                 span_particles: int = 0, graph: bool = False,
                  stream=None, workspace: str = "torch", gas: Optional[dict] = None):
         L = load_library()
         self._lib = L
@@ -153,6 +176,7 @@ class Dsmc:
         o = default_options()
         o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
         o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
+        o.span_particles, o.graph = int(span_particles), int(bool(graph))
         self._ws = None
         if workspace == "torch":
             import torch
@@ -249,6 +273,165 @@ class Dsmc:
         i = Info()
         _check(self._lib.dsmc_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def kernel_times(self) -> dict:
+        n = self._lib.dsmc_kernel_count()
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.int64)
+        _check(self._lib.dsmc_kernel_times(self._h, _ptr(ms), _ptr(cnt)))
+        return {self._lib.dsmc_kernel_name(k).decode(): (float(ms[k]), int(cnt[k]))
+                for k in range(n)}
+
+    def reset_kernel_times(self) -> None:
+        _check(self._lib.dsmc_reset_kernel_times(self._h))
+
+
+def make_instance(Kn: float, n_cells: int, ppc: int, *, omega: float = 0.5,
+                  body_force: float = 0.0, seed: int = 0, wall_T: float = 273.0,
+                  gas: Optional[dict] = None) -> Instance:
+    g = dict(ARGON)
+    g.update(gas or {})
+    return Instance(Gas(g["mass"], g["d_ref"], float(omega), g["T_ref"]), float(Kn),
+                    float(wall_T), float(body_force), int(n_cells), int(ppc),
+                    int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+class DsmcBatch:
+    """Many independent DSMC runs advanced by the same launches (``dsmc_create_batch``).
+
+    ``instances``: a sequence of dicts with the keyword arguments of ``make_instance``
+    (Kn, n_cells, ppc, omega, body_force, seed, wall_T).  Options are shared.  Instance
+    i evolves exactly as ``Dsmc(**instances[i], ...)`` with the same options.
+    """
+
+    def __init__(self, instances, *, dt_factor: float = 0.2, dt: float = 0.0,
+                 sample_start: int = 0, group_size: int = 256, collisions: bool = True,
+                 profile: bool = False, span_particles: int = 0, graph: bool = False,
+                 stream=None, workspace: str = "torch"):
+        L = load_library()
+        self._lib = L
+        self._defs = [dict(d) for d in instances]
+        arr = (Instance * len(self._defs))(*[make_instance(**d) for d in self._defs])
+        self._arr = arr
+        self.n = len(self._defs)
+        self.n_cells = [int(d["n_cells"]) for d in self._defs]
+        self.ppc = [int(d["ppc"]) for d in self._defs]
+        self.cell_base = np.concatenate([[0], np.cumsum(self.n_cells)]).astype(np.int64)
+        o = default_options()
+        o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
+        o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
+        o.span_particles, o.graph = int(span_particles), int(bool(graph))
+        self._ws = None
+        if workspace == "torch":
+            import torch
+            nbytes = L.dsmc_batch_workspace_bytes(arr, self.n)
+            if nbytes == 0:
+                raise DsmcError(1, "invalid instance sizes")
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+            ws_ptr, ws_bytes = self._ws.data_ptr(), nbytes
+        elif workspace == "library":
+            ws_ptr, ws_bytes = None, 0
+        else:
+            raise ValueError("workspace must be 'torch' or 'library'")
+        o.stream = int(stream) if stream is not None else None
+        self._opt = o
+        h = ctypes.c_void_p()
+        _check(L.dsmc_create_batch(arr, self.n, ctypes.byref(o), ws_ptr, ws_bytes,
+                                   ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.dsmc_destroy(self._h)
+            self._h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, n: int = 1) -> None:
+        _check(self._lib.dsmc_step(self._h, int(n)))
+
+    def sync(self) -> None:
+        _check(self._lib.dsmc_sync(self._h))
+
+    def set_options(self, **kw) -> None:
+        o = Options.from_buffer_copy(self._opt)
+        for k, v in kw.items():
+            if k == "stream":
+                v = int(v) if v is not None else None
+            setattr(o, k, v)
+        _check(self._lib.dsmc_set_options(self._h, ctypes.byref(o)))
+        self._opt = o
+
+    def autotune(self, steps_per_trial: int = 4):
+        best = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(self._lib.dsmc_autotune(self._h, int(steps_per_trial), ctypes.byref(best),
+                                       ctypes.byref(ms)))
+        self._opt.span_particles = best.value
+        return best.value, ms.value
+
+    def moments(self, i: int, out=None):
+        if out is None:
+            out = np.empty((self.n_cells[i], NMOM), np.float64)
+        ns = ctypes.c_longlong()
+        _check(self._lib.dsmc_sample_moments_of(self._h, int(i), _ptr(out), ctypes.byref(ns)))
+        return out, int(ns.value)
+
+    def moments_all(self, out=None):
+        """(raw sums [sum n_cells, 13], sampled steps per instance); rows of instance i
+        are ``cell_base[i]:cell_base[i+1]``."""
+        if out is None:
+            out = np.empty((int(self.cell_base[-1]), NMOM), np.float64)
+        ns = np.empty(self.n, np.int64)
+        _check(self._lib.dsmc_sample_moments_all(self._h, _ptr(out), _ptr(ns)))
+        return out, ns
+
+    def reset_samples(self, i: Optional[int] = None) -> None:
+        if i is None:
+            _check(self._lib.dsmc_reset_samples(self._h))
+        else:
+            _check(self._lib.dsmc_reset_samples_of(self._h, int(i)))
+
+    def state(self, i: int):
+        n = self.n_cells[i] * self.ppc[i]
+        arrs = [np.empty(n, np.float32) for _ in range(4)]
+        _check(self._lib.dsmc_copy_state_of(self._h, int(i), *[_ptr(a) for a in arrs]))
+        return tuple(arrs)
+
+    def cells(self, i: int):
+        nc = self.n_cells[i]
+        off = np.empty(nc + 1, np.int32)
+        smax = np.empty(nc, np.float32)
+        cand = np.empty(nc, np.uint64)
+        acc = np.empty(nc, np.uint64)
+        _check(self._lib.dsmc_copy_cells_of(self._h, int(i), _ptr(off), _ptr(smax), _ptr(cand),
+                                            _ptr(acc)))
+        return off, smax, cand, acc
+
+    def load_state(self, i: int, y, vx, vy, vz, smax=None, step: int = 0) -> None:
+        arrs = [np.ascontiguousarray(a, np.float32) if isinstance(a, np.ndarray) else a
+                for a in (y, vx, vy, vz)]
+        sm = None if smax is None else np.ascontiguousarray(smax, np.float32)
+        _check(self._lib.dsmc_load_state_of(self._h, int(i), *[_ptr(a) for a in arrs],
+                                            _ptr(sm), int(step)))
+
+    def info(self, i: int = 0) -> dict:
+        inf = Info()
+        _check(self._lib.dsmc_get_info_of(self._h, int(i), ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
 
     def kernel_times(self) -> dict:
         n = self._lib.dsmc_kernel_count()

@@ -42,8 +42,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_default_options(lib):
     o = D.default_options()
-    assert (o.dt_factor, o.dt, o.sample_start, o.group_size, o.collisions, o.profile) == \
-        (0.2, 0.0, 0, 256, 1, 0)
+    assert (o.dt_factor, o.dt, o.sample_start, o.group_size, o.collisions, o.profile,
+            o.span_particles, o.graph) == (0.2, 0.0, 0, 256, 1, 0, 0, 0)
     assert lib.dsmc_kernel_count() == 7
     assert lib.dsmc_kernel_name(0) == b"init"
     assert lib.dsmc_status_string(4) == b"device limit reached"
@@ -84,17 +84,55 @@ def test_bad_gas_and_options_rejected(lib):
     st, msg = _create(lib, gas=D.Gas(-1.0, 4.17e-10, 0.5, 273.0))
     assert st == 1 and "mass" in msg
     for field, val in (("group_size", 3), ("group_size", 1024), ("dt_factor", 0.0),
-                       ("dt", -1.0)):
+                       ("dt", -1.0), ("span_particles", 1000), ("span_particles", 1 << 25),
+                       ("graph", 1)):
         o = D.default_options()
         setattr(o, field, val)
         st, msg = _create(lib, opt=o)
         assert st == 1 and "options" in msg, (field, msg)
 
 
+def _batch(lib, defs, opt=None):
+    arr = (D.Instance * len(defs))(*[D.make_instance(**d) for d in defs])
+    h = ctypes.c_void_p()
+    o = D.default_options() if opt is None else opt
+    st = lib.dsmc_create_batch(arr, len(defs), ctypes.byref(o), None, 0, ctypes.byref(h))
+    return st, lib.dsmc_last_error().decode()
+
+
+def test_batch_arguments_are_rejected(lib):
+    ok = dict(Kn=1.0, n_cells=10, ppc=10)
+    st, msg = _batch(lib, [ok, dict(ok, Kn=-1.0)])
+    assert st == 1 and "instance 1" in msg and "Kn" in msg
+    st, msg = _batch(lib, [ok, ok, dict(ok, n_cells=20000)])
+    assert st == 1 and "instance 2" in msg and "16384" in msg
+    # each instance alone is within limits, together they are not
+    big = dict(Kn=1.0, n_cells=10000, ppc=150000)
+    st, msg = _batch(lib, [big, big])
+    assert st == 1 and "total" in msg
+    h = ctypes.c_void_p()
+    assert lib.dsmc_create_batch(None, 1, None, None, 0, ctypes.byref(h)) == 1
+    arr = (D.Instance * 1)(D.make_instance(**ok))
+    assert lib.dsmc_create_batch(arr, 0, None, None, 0, ctypes.byref(h)) == 1
+
+
+def test_batch_workspace_is_the_sum_of_its_parts(lib):
+    defs = [dict(Kn=1.0, n_cells=50 + 7 * i, ppc=40 + 3 * i) for i in range(5)]
+    arr = (D.Instance * 5)(*[D.make_instance(**d) for d in defs])
+    total = lib.dsmc_batch_workspace_bytes(arr, 5)
+    singles = sum(lib.dsmc_workspace_bytes(d["n_cells"], d["ppc"]) for d in defs)
+    assert total > 0 and total <= singles
+    assert total >= sum(2 * 16 * d["n_cells"] * d["ppc"] for d in defs)
+    assert lib.dsmc_batch_workspace_bytes(arr, 0) == 0
+    assert lib.dsmc_batch_size(None) == 0
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.dsmc_step(None, 1) == 1
     assert lib.dsmc_sync(None) == 1
     assert lib.dsmc_destroy(None) == 0
+    assert lib.dsmc_autotune(None, 1, None, None) == 1
+    assert lib.dsmc_sample_moments_of(None, 0, None, None) == 1
 
 
 def test_missing_library_fails_loudly(tmp_path):
