@@ -5,7 +5,9 @@ one JSON line on stdout.
 
 A step is one DSMC time step over every particle: collisions with the symmetric
 moment sample, free flight with the body force and the walls, and the stable cell
-sort (five kernel launches).  The particle state (1.6 GB with its sort buffer) is
+sort (four kernel launches).  The line also carries, under "batched", the
+256-instance batched workload (one batch handle, tuned span partition, CUDA-graph
+replay) against the same instances stepped one after another as single runs.  The particle state (1.6 GB with its sort buffer) is
 resident in HBM and larger than L2, so no flush is needed between steps.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
@@ -227,6 +229,155 @@ def config_dict(w, n_gpus):
             "l2": "inputs larger than L2 (1.6 GB resident state vs 129 MB L2)"}
 
 
+def batch_defs(n: int = 256):
+    return [dict(Kn=w.Kn, n_cells=w.n_cells, ppc=w.ppc, omega=w.omega,
+                 body_force=w.body_force, seed=w.seeds[0]) for w in W.batch_instances(n)]
+
+
+def run_batched(steps: int, warmup: int, rank: int) -> dict:
+    """The 256-instance batched workload (Kn log-uniform in [0.05, 10], 50-1000 cells,
+    50-400 particles per cell, force 0.5-2 x the Kn = 1 force): one batch handle with
+    the tuned span partition, steps replayed as CUDA graphs, against the same instances
+    stepped one after another as plain single runs."""
+    import torch
+    from paper_2311_14140_gb300 import Dsmc, DsmcBatch
+    defs = batch_defs()
+    if rank:
+        for d in defs:
+            d["seed"] += rank << 32
+    n_part = sum(d["n_cells"] * d["ppc"] for d in defs)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        b = DsmcBatch(defs, sample_start=1, graph=True, stream=side.cuda_stream)
+        best, tuned_ms = b.autotune(steps_per_trial=3)
+        b.step(max(warmup, 16))
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        b.step(steps)
+        e1.record(side)
+        side.synchronize()
+        t_batch = e0.elapsed_time(e1) / 1e3
+        # kernel shares of the same steps launched directly with timing events
+        b.set_options(profile=True, graph=False)
+        b.reset_kernel_times()
+        b.step(8)
+        kt = b.kernel_times()
+        info = b.info(0)
+        b.close()
+        del b
+    torch.cuda.synchronize()
+    # The same instances as separate plain runs, stepped one after another.
+    runs = [Dsmc(sample_start=1, **d) for d in defs]
+    stream = torch.cuda.current_stream()
+    for r in runs:
+        r.step(warmup)
+    torch.cuda.synchronize()
+    seq_steps = max(1, min(steps, 20))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in runs:
+        r.step(seq_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    for r in runs:
+        r.close()
+    del runs
+    torch.cuda.synchronize()
+    ms_cm, n_cm = kt.get("collide_move", (0.0, 0))
+    tot = sum(v[0] for v in kt.values())
+    peak, peak_kind = peaks()
+    value = n_part * steps / t_batch
+    return {
+        "workload": "batch256: Kn log-uniform [0.05,10], 50-1000 cells, 50-400 ppc, HS argon",
+        "n_instances": len(defs), "n_particles": n_part, "steps": steps,
+        "value": value, "unit": METRIC, "ms_per_step": 1e3 * t_batch / steps,
+        "instance_steps_per_s": len(defs) * steps / t_batch,
+        "span_particles": best, "graph_replay": True,
+        "effective_step": {"bytes_per_particle_step": 32,
+                           "gbs": 32.0 * value / 1e9, "frac": 32.0 * value / 1e9 / peak,
+                           "peak_kind": peak_kind},
+        "collide_move_share": ms_cm / tot if tot else None,
+        "collide_move_gbs": (32.0 * n_part / (ms_cm / 1e3 / n_cm) / 1e9) if n_cm else None,
+        "sequential_single_runs": {"value": n_part * seq_steps / t_seq, "unit": METRIC,
+                                   "ms_per_step": 1e3 * t_seq / seq_steps,
+                                   "steps": seq_steps},
+        "speedup_vs_sequential": (n_part * steps / t_batch) / (n_part * seq_steps / t_seq),
+        "cells_per_span_instance0": info["cells_per_span"],
+    }
+
+
+def run_serve(args, world, rank, local):
+    """Serving workload: Poisson arrivals of micro-solve requests drawn as the batched
+    workload, each run to a relative standard error of its channel-mean velocity, through
+    the library's request loop on one pool (continuous batching); beside it, the same
+    requests solved one at a time as plain runs (a sample of them)."""
+    import numpy as np
+    import torch
+    from paper_2311_14140_gb300 import DsmcPool, _build, solve
+    _build.build()
+    torch.cuda.set_device(local)
+    reqs = W.serving_requests(args.requests, args.rate, args.target_se,
+                              seed=4242 + 1000 * rank)
+    side = torch.cuda.Stream()
+    clocks = Clocks(local)
+    with torch.cuda.stream(side):
+        pool = DsmcPool(max_particles=args.pool_particles, max_cells=args.pool_particles // 50,
+                        max_instances=4096, max_cells_per_instance=1000,
+                        sample_start=args.warmup_steps, graph=True, stream=side.cuda_stream)
+        barrier(world)
+        clocks.start()
+        t0 = time.perf_counter()
+        res = pool.serve(reqs, epoch_steps=32, batches=16)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        pool.close()
+    done = [r for r in res if r["finished"] >= 0 and r["converged"] >= 0]
+    lat = np.array([r["finished"] - q["arrival"] for r, q in zip(res, reqs)
+                    if r["finished"] >= 0 and r["converged"] >= 0])
+    qwait = np.array([r["admitted"] - q["arrival"] for r, q in zip(res, reqs)
+                      if r["admitted"] >= 0])
+    psteps = sum(r["steps"] * q["n_cells"] * q["ppc"] for r, q in zip(res, reqs))
+    # The same kind of requests one at a time as plain runs.
+    seq = []
+    t1 = time.perf_counter()
+    for q in reqs[:args.sequential_sample]:
+        seq.append(solve(q, epoch_steps=32, batches=16, sample_start=args.warmup_steps))
+    t_seq = time.perf_counter() - t1
+    seq_psteps = sum(r["steps"] * q["n_cells"] * q["ppc"]
+                     for r, q in zip(seq, reqs[:args.sequential_sample]))
+    solves_per_s = len(done) / wall
+    line = {
+        "metric": "micro-solves/s", "value": world * solves_per_s, "unit": "micro-solves/s",
+        "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals, requests drawn as batch256",
+                   "requests": args.requests, "rate_per_s": args.rate,
+                   "target_se": args.target_se, "warmup_steps": args.warmup_steps,
+                   "pool_particles": args.pool_particles, "epoch_steps": 32,
+                   "se_batches": 16, "parallelism": f"replicas x{world}"},
+        "wall_s": wall, "finished": len(done),
+        "converged": sum(1 for r in res if r["converged"] == 1),
+        "latency_s": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
+                      "p99": float(np.percentile(lat, 99)) if lat.size else None,
+                      "max": float(lat.max()) if lat.size else None},
+        "queue_wait_s": {"p50": float(np.percentile(qwait, 50)) if qwait.size else None,
+                         "p99": float(np.percentile(qwait, 99)) if qwait.size else None},
+        "particle_steps_per_s": psteps / wall,
+        "sequential_plain_solves": {
+            "requests": len(seq), "seconds": t_seq,
+            "solves_per_s": len(seq) / t_seq if t_seq > 0 else None,
+            "particle_steps_per_s": seq_psteps / t_seq if t_seq > 0 else None},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -313,6 +464,8 @@ def run_ours(args, world, rank, local):
                             "read into pinned host memory after every step"},
         "gpu_launches": launches,
     }
+    if not args.no_batched:
+        result["batched"] = run_batched(args.steps, args.warmup, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_sample()
     if rank == 0:
@@ -327,6 +480,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256-instance batched measurement")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the serving workload instead (its own JSON line)")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--target-se", type=float, default=0.05)
+    ap.add_argument("--warmup-steps", type=int, default=256)
+    ap.add_argument("--pool-particles", type=int, default=64_000_000)
+    ap.add_argument("--sequential-sample", type=int, default=8)
     ap.add_argument("--cells", type=int, default=None,
                     help="override the cell count (profiling cases only)")
     ap.add_argument("--ppc", type=int, default=None,
@@ -341,6 +504,8 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, world, rank)
+        if args.serve:
+            return run_serve(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

@@ -125,6 +125,7 @@ typedef struct dsmc_info {
   int n_spans;         /* this instance's spans (CTAs of the collide/move pass) */
   int total_spans;     /* spans of all instances */
   int first_slot;      /* the instance's first particle slot in the handle */
+  int first_cell;      /* the instance's first row in dsmc_sample_moments_all */
 } dsmc_info;
 
 /* One member of a batch: the arguments of dsmc_create. */
@@ -235,10 +236,11 @@ DSMC_API dsmc_status dsmc_create_batch(const dsmc_instance* instances, int n_ins
                                        const dsmc_options* opt, void* workspace,
                                        size_t workspace_bytes, dsmc_handle* out);
 
-/* Number of instances (0 for NULL). */
+/* Number of active instances (0 for NULL). */
 DSMC_API int dsmc_batch_size(dsmc_handle h);
 
-/* Per-instance forms of the functions above, instance index 0 <= i < batch size. */
+/* Per-instance forms of the functions above, for instance id i (0 <= i < batch size for
+ * dsmc_create_batch; the id from dsmc_pool_add for pools). */
 DSMC_API dsmc_status dsmc_sample_moments_of(dsmc_handle h, int i, double* out,
                                             long long* n_samples);
 DSMC_API dsmc_status dsmc_reset_samples_of(dsmc_handle h, int i);
@@ -252,10 +254,101 @@ DSMC_API dsmc_status dsmc_load_state_of(dsmc_handle h, int i, const float* y, co
                                         long long step);
 DSMC_API dsmc_status dsmc_get_info_of(dsmc_handle h, int i, dsmc_info* info);
 
-/* The moment sums of all instances in one copy: out holds sum(n_cells_i) x DSMC_NMOM
- * binary64 values, instance after instance; n_samples (NULL or batch-size entries)
- * gets each instance's sampled steps.  Synchronises. */
+/* The moment sums of all instances in one copy: out holds (cell capacity of the
+ * handle) x DSMC_NMOM binary64 values; instance i's rows start at its
+ * dsmc_info.first_cell (for dsmc_create_batch: instance after instance, no gaps).
+ * n_samples (NULL or dsmc_id_bound entries) gets each instance's sampled steps (0 for
+ * unused ids).  Synchronises. */
 DSMC_API dsmc_status dsmc_sample_moments_all(dsmc_handle h, double* out, long long* n_samples);
+
+/* One more than the largest instance id the handle has handed out. */
+DSMC_API int dsmc_id_bound(dsmc_handle h);
+
+/* Per instance id < dsmc_id_bound: out[2 id] = sampled particle count and
+ * out[2 id + 1] = sum of vx over all cells and sampled steps (zeros for unused ids).
+ * The channel-mean velocity of the samples is their ratio.  Synchronises. */
+DSMC_API dsmc_status dsmc_channel_sums(dsmc_handle h, double* out);
+
+/* Pools: a handle whose instances come and go while it runs (continuous batching).
+ * Capacity is fixed at creation; dsmc_pool_add places an instance in free ranges of
+ * the handle's arrays (DSMC_E_NOMEM "no room" when they are taken) and
+ * dsmc_pool_remove frees them.  An added instance is set up on the device by the next
+ * dsmc_step or synchronising call, exactly as dsmc_create would set it up, and from
+ * then on evolves as it would alone (the counter-based random numbers are keyed on its
+ * own seed, step, cells and slots).  Removal takes effect for the next launch; work
+ * already enqueued finishes first.  Ids of removed instances are reused.  Options are
+ * shared by all instances; sample_start counts each instance's own steps. */
+typedef struct dsmc_pool_limits {
+  long long max_particles;    /* slots, each instance padded to a multiple of 64 */
+  int max_cells;              /* cells of all instances together */
+  int max_instances;          /* instances at once, 1..65535 */
+  int max_cells_per_instance; /* 1..16384 */
+} dsmc_pool_limits;
+
+/* Device bytes dsmc_pool_create needs (0 for invalid limits). */
+DSMC_API size_t dsmc_pool_workspace_bytes(const dsmc_pool_limits* limits);
+DSMC_API dsmc_status dsmc_pool_create(const dsmc_pool_limits* limits, const dsmc_options* opt,
+                                      void* workspace, size_t workspace_bytes,
+                                      dsmc_handle* out);
+/* *id gets the new instance's id (-1 on failure). */
+DSMC_API dsmc_status dsmc_pool_add(dsmc_handle h, const dsmc_instance* instance, int* id);
+DSMC_API dsmc_status dsmc_pool_remove(dsmc_handle h, int id);
+
+/* Serving: micro-solve requests run to a target standard error.
+ *
+ * A request is one run (dsmc_instance) that arrives at `arrival` seconds after the
+ * start of dsmc_serve and is finished when the relative standard error of its
+ * channel-mean velocity (sum vx / count over all sampled particles and steps) is at
+ * most target_se, or after max_steps steps.  The standard error is taken by batch means:
+ * the sampled epochs (epoch_steps steps each, sampling from the pool's
+ * options.sample_start on, counted in each instance's own steps) are split into
+ * `batches` consecutive batches, each gives a mean, and the error is their standard
+ * deviation over sqrt(batches).  The paper runs its micro-solves at the (Kn, force)
+ * points its surrogate asks for (Sec. 2.3-2.4); the request loop is this library's. */
+typedef struct dsmc_request {
+  dsmc_instance instance;
+  double arrival;      /* seconds after the start, non-decreasing along the array */
+  double target_se;    /* relative standard error to reach, > 0 (0.01 = 1 %) */
+  long long max_steps; /* >= 1 */
+} dsmc_request;
+
+typedef struct dsmc_serve_options {
+  int epoch_steps;   /* steps between reads of the channel sums; default 32 */
+  int batches;       /* batches of the batch-means error, >= 2; default 16 */
+  int max_active;    /* instances on the device at once, 0: as many as fit; default 0 */
+  double time_limit; /* seconds, 0: none; default 0 */
+} dsmc_serve_options;
+
+typedef struct dsmc_request_result {
+  double admitted;   /* seconds after the start (-1: never admitted) */
+  double finished;   /* seconds after the start (-1: not finished in the time limit) */
+  long long steps;   /* steps run */
+  double u_mean;     /* channel-mean velocity of the samples (v0) */
+  double u_se;       /* its batch-means standard error (v0); INFINITY if too few epochs */
+  double count;      /* final channel sums: sampled particle count ... */
+  double sum_vx;     /* ... and sum of vx */
+  int converged;     /* 1 target met, 0 step or time limit, -1 rejected (invalid or too
+                        large for the pool) */
+  int id;            /* pool id it ran under */
+} dsmc_request_result;
+
+DSMC_API dsmc_status dsmc_default_serve_options(dsmc_serve_options* so);
+
+/* Continuous batching of `requests` on an empty pool handle (dsmc_pool_create), in
+ * real time: a request is admitted once it has arrived and the pool has room (in
+ * order of arrival), all admitted instances advance together epoch_steps at a time,
+ * and every instance whose target is met after an epoch is removed, its result
+ * recorded, and its memory given to the next waiting requests.  Each instance's
+ * trajectory is that of the same run alone.  results[n_requests] are filled.
+ * Returns when every request is finished or the time limit has passed. */
+DSMC_API dsmc_status dsmc_serve(dsmc_handle pool, const dsmc_request* requests, int n_requests,
+                                const dsmc_serve_options* so, dsmc_request_result* results);
+
+/* One request solved as a plain run of its own (dsmc_create_in with `opt`, the library
+ * allocating), epoch by epoch to the same criterion; times are seconds after the call
+ * (admitted: after creation).  For comparison with dsmc_serve. */
+DSMC_API dsmc_status dsmc_solve(const dsmc_request* request, const dsmc_options* opt,
+                                const dsmc_serve_options* so, dsmc_request_result* result);
 
 /* Tuner of the step partition.  For span sizes 1024, 2048, ... particles (those whose
  * shared memory fits, skipping sizes that give the same partition) it runs one

@@ -2,12 +2,13 @@
 micro model of the Micro-Macro-Surrogate method of arXiv 2311.14140.
 
 ``Dsmc`` wraps the C ABI of ``include/dsmc.h`` (CUDA kernels in ``csrc/``) for one
-run, ``DsmcBatch`` for many independent runs advanced by the same launches;
+run, ``DsmcBatch`` for many independent runs advanced by the same launches,
+``DsmcPool`` for runs that come and go (continuous batching, ``DsmcPool.serve``);
 ``fields`` turns raw moment sums into cell fields; ``workloads`` names the synthetic
 runs.  Build the library with ``__graft_entry__.build()`` or ``_build.build()``.
 """
-from .dsmc import (Dsmc, DsmcBatch, DsmcError, Options, default_options, fields,  # noqa: F401
-                   load_library)
+from .dsmc import (Dsmc, DsmcBatch, DsmcError, DsmcPool, Options, default_options,  # noqa: F401
+                   fields, load_library, solve)
 
-__all__ = ["Dsmc", "DsmcBatch", "DsmcError", "Options", "default_options", "fields",
-           "load_library"]
+__all__ = ["Dsmc", "DsmcBatch", "DsmcError", "DsmcPool", "Options", "default_options",
+           "fields", "load_library", "solve"]

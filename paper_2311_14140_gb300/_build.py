@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libdsmc.so")
-SOURCES = ["dsmc_kernels.cu", "dsmc_step.cu", "dsmc_capi.cu", "dsmc_noalloc.cu"]
+SOURCES = ["dsmc_kernels.cu", "dsmc_step.cu", "dsmc_capi.cu", "dsmc_noalloc.cu",
+           "dsmc_serve.cu"]
 HEADERS = ["dsmc_device.cuh", "dsmc_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -6,8 +6,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -148,73 +150,153 @@ struct DeviceGuard {
   }
 };
 
-// One instance of a run: its definition, derived parameters, place in the
-// concatenated device arrays, span partition and counters.
+// First-fit allocator of index ranges [0, capacity) (slots, cells, cell offsets and
+// sort-matrix entries of the instances of a handle).
+class Extents {
+ public:
+  void reset(long long capacity) {
+    free_.clear();
+    if (capacity > 0) free_[0] = capacity;
+  }
+  long long alloc(long long n) {
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= n) {
+        const long long s = it->first, len = it->second;
+        free_.erase(it);
+        if (len > n) free_[s + n] = len - n;
+        return s;
+      }
+    return -1;
+  }
+  void release(long long s, long long n) {
+    auto it = free_.emplace(s, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<long long, long long> free_;
+};
+
+// One instance of a run: its definition, derived parameters, place in the device
+// arrays, span partition and counters.
 struct Inst {
+  bool active = false;
+  bool fresh = false;  // added, not yet initialised on the device
   double omega = 0.5, Kn = 1.0, wall_T = 273.0, F = 0.0;
   int n_cells = 0, ppc = 0;
   long long N = 0;
   uint64_t seed = 0;
   Params p{};
   int max_spans = 0;  // rows of the sort matrix reserved (finest partition)
+  long long slot_len = 0;
   int part_base = 0, cell_base = 0, off_base = 0;
   long long hist_base = 0;
   int cps = 0, n_spans = 0, span_base = 0;  // partition in use
   long long step = 0, n_samples = 0;
 };
 
-// Byte offsets of the arrays in the device workspace.
-struct Layout {
-  long long n_slots = 0, hist_ints = 0;
-  int cells = 0, offs = 0, max_spans = 0, max_cells = 0;
-  size_t st, hist, count, offset, smax, ncand, nacc, acc, tab, span_inst, err, total;
+// Sizes of the device arrays of a handle.
+struct Capacity {
+  long long slots = 0, hist_ints = 0;
+  int cells = 0, offs = 0, spans = 0, inst = 0;
 };
 
-// Concatenates the instances: slots (each instance padded to 64), cells, cell
-// offsets (n_cells + 1 each) and sort-matrix rows, and sizes the workspace.
-Layout place(std::vector<Inst>& v) {
+// Byte offsets of the arrays in the device workspace.
+struct Layout {
+  size_t st, hist, count, offset, smax, ncand, nacc, acc, tab, span_inst, chan, err, total;
+};
+
+long long padded_slots(long long N) { return (N + 63) & ~63LL; }
+
+int reserved_spans(int n_cells, int ppc) {
+  int cps, ns;
+  make_spans(n_cells, ppc, kMinSpanParticles, &cps, &ns);
+  return ns;
+}
+
+// Workspace layout for a capacity: two record buffers, the sort matrix, per-cell
+// arrays, two instance tables and two span tables (the step's and the admission
+// pass's), the channel sums and the error word.
+Layout layout_of(const Capacity& C) {
   Layout L{};
-  for (size_t i = 0; i < v.size(); ++i) {
-    Inst& x = v[i];
-    int cps, ns;
-    make_spans(x.n_cells, x.ppc, kMinSpanParticles, &cps, &ns);
-    x.max_spans = ns;
-    x.part_base = (int)L.n_slots;
-    x.cell_base = L.cells;
-    x.off_base = L.offs;
-    x.hist_base = L.hist_ints;
-    L.n_slots += (x.N + 63) & ~63LL;
-    L.cells += x.n_cells;
-    L.offs += x.n_cells + 1;
-    L.hist_ints += (long long)ns * x.n_cells;
-    L.max_spans += ns;
-    L.max_cells = std::max(L.max_cells, x.n_cells);
-  }
   size_t o = 0;
   L.st = o;
-  o += align256(2 * (size_t)L.n_slots * sizeof(float4));
+  o += align256(2 * (size_t)C.slots * sizeof(float4));
   L.hist = o;
-  o += align256((size_t)L.hist_ints * sizeof(int));
+  o += align256((size_t)C.hist_ints * sizeof(int));
   L.count = o;
-  o += align256((size_t)L.cells * sizeof(int));
-  L.offset = o;  // two arrays: current and next
-  o += align256(2 * (size_t)L.offs * sizeof(int));
+  o += align256((size_t)C.cells * sizeof(int));
+  L.offset = o;
+  o += align256(2 * (size_t)C.offs * sizeof(int));
   L.smax = o;
-  o += align256(2 * (size_t)L.cells * sizeof(float));
+  o += align256(2 * (size_t)C.cells * sizeof(float));
   L.ncand = o;
-  o += align256((size_t)L.cells * sizeof(unsigned long long));
+  o += align256((size_t)C.cells * sizeof(unsigned long long));
   L.nacc = o;
-  o += align256((size_t)L.cells * sizeof(unsigned long long));
+  o += align256((size_t)C.cells * sizeof(unsigned long long));
   L.acc = o;
-  o += align256((size_t)L.cells * kNMom * sizeof(double));
+  o += align256((size_t)C.cells * kNMom * sizeof(double));
   L.tab = o;
-  o += align256(v.size() * sizeof(InstParams));
+  o += align256(2 * (size_t)C.inst * sizeof(InstParams));
   L.span_inst = o;
-  o += align256((size_t)L.max_spans * sizeof(int));
+  o += align256(2 * (size_t)C.spans * sizeof(int));
+  L.chan = o;
+  o += align256(2 * (size_t)C.inst * sizeof(double));
   L.err = o;
   o += 256;
   L.total = o;
   return L;
+}
+
+// The capacity that holds exactly these instances, placed one after another.
+Capacity capacity_of(const dsmc_instance* d, int n) {
+  Capacity C{};
+  for (int i = 0; i < n; ++i) {
+    const long long N = (long long)d[i].n_cells * d[i].ppc;
+    const int rows = reserved_spans(d[i].n_cells, d[i].ppc);
+    C.slots += padded_slots(N);
+    C.cells += d[i].n_cells;
+    C.offs += d[i].n_cells + 1;
+    C.hist_ints += (long long)rows * d[i].n_cells;
+    C.spans += rows;
+  }
+  C.inst = n;
+  return C;
+}
+
+// The capacity of a pool: every instance of `lim` fits as long as the totals do (up to
+// fragmentation of the free ranges).
+dsmc_status capacity_of_pool(const dsmc_pool_limits* lim, Capacity* C) {
+  if (!lim) return fail(DSMC_E_INVAL, "pool limits: NULL");
+  if (lim->max_particles < 1 || lim->max_particles > kMaxParticles || lim->max_cells < 1 ||
+      lim->max_instances < 1 || lim->max_instances > kMaxInstances ||
+      lim->max_cells_per_instance < 1 || lim->max_cells_per_instance > kMaxStepCells ||
+      lim->max_cells_per_instance > lim->max_cells)
+    return fail(DSMC_E_INVAL,
+                "pool limits: max_particles 1..2^31 - 2^24, max_instances 1..65535, "
+                "1 <= max_cells_per_instance <= min(16384, max_cells)");
+  Capacity c{};
+  c.slots = lim->max_particles;
+  c.cells = lim->max_cells;
+  c.offs = lim->max_cells + lim->max_instances;
+  c.inst = lim->max_instances;
+  // An instance of N particles reserves at most N / 1024 + 1 sort-matrix rows.
+  const long long rows = lim->max_particles / kMinSpanParticles + lim->max_instances;
+  c.spans = (int)std::min<long long>(rows, INT_MAX / 2);
+  c.hist_ints = rows * (long long)lim->max_cells_per_instance;
+  *C = c;
+  return DSMC_OK;
 }
 
 // Checks one instance definition; the message names the instance in a batch.
@@ -243,12 +325,17 @@ void dsmc::set_last_error(const std::string& msg) { g_last_error = msg; }
 
 struct dsmc_sim {
   int device = 0;
+  bool pool = false;  // instances may be added and removed
   dsmc_options opt{};
-  std::vector<Inst> inst;
-  long long gstep = 0;  // steps this handle has launched
+  std::vector<Inst> inst;  // by id
+  std::vector<int> order;  // active ids in table order
+  long long gstep = 0;     // steps this handle has launched
   int span_target = kDefaultSpanParticles;
-  int spans = 0, max_cps = 0;  // partition in use
+  int spans = 0, max_cps = 1, max_cells = 1;  // partition in use
+  int spans_reserved = 0;
+  Capacity C{};
   Layout L{};
+  Extents ex_slots, ex_cells, ex_offs, ex_hist;
   void* ws = nullptr;
   bool owns = false;
   float4* P[2]{};  // particle records (y, vx, vy, vz), double-buffered for the sort
@@ -260,10 +347,11 @@ struct dsmc_sim {
   int scur = 0;
   unsigned long long *ncand = nullptr, *nacc = nullptr;
   double* acc = nullptr;
-  InstParams* tab_dev = nullptr;
-  int* span_inst_dev = nullptr;
-  std::vector<InstParams> tab;
-  std::vector<int> span_inst;
+  InstParams* tab_dev = nullptr;  // [0, C.inst): the step's; [C.inst, 2 C.inst): admission
+  int* span_inst_dev = nullptr;   // likewise with C.spans entries each
+  double* chan_dev = nullptr;
+  std::vector<InstParams> tab, adm_tab;
+  std::vector<int> span_inst, adm_span;
   bool tab_dirty = true, spans_dirty = true;
   // CUDA graph of kGraphSteps consecutive steps, replayed by dsmc_step when
   // options.graph is set.  Its kernels read the global step from gstep_dev, which the
@@ -280,7 +368,7 @@ struct dsmc_sim {
   long long kcount[K_NUM] = {};
 
   cudaStream_t stream() const { return (cudaStream_t)opt.stream; }
-  int n_inst() const { return (int)inst.size(); }
+  int n_inst() const { return (int)order.size(); }
   int cap() const { return opt.group_size + opt.group_size / 2 - 1; }
 };
 
@@ -332,42 +420,51 @@ bool step_fits(int max_cells, int max_cps, int G) {
   return step_smem_layout(max_cells, max_cps, G + G / 2 - 1).total <= kStepSmemMax;
 }
 
-// The largest cells-per-span any instance would use with `target` particles per span.
-int partition_max_cps(const dsmc_sim* h, int target) {
-  int m = 1;
-  for (const Inst& x : h->inst) {
+// The largest cells-per-span any active instance (and `extra`, if given) would use
+// with `target` particles per span, and the largest cell count.
+void partition_extent(const dsmc_sim* h, int target, const Inst* extra, int* max_cps,
+                      int* max_cells) {
+  int m = 1, mc = 1;
+  auto visit = [&](const Inst& x) {
     int cps, ns;
     make_spans(x.n_cells, x.ppc, target, &cps, &ns);
     m = std::max(m, cps);
-  }
-  return m;
+    mc = std::max(mc, x.n_cells);
+  };
+  for (int id : h->order) visit(h->inst[id]);
+  if (extra) visit(*extra);
+  *max_cps = m;
+  *max_cells = mc;
 }
 
-// Assigns spans with `target` particles per span to every instance.
+// Assigns spans with `target` particles per span to every active instance.
 void set_partition(dsmc_sim* h, int target) {
   h->span_target = target;
   h->span_inst.clear();
-  int base = 0, m = 1;
-  for (int i = 0; i < h->n_inst(); ++i) {
-    Inst& x = h->inst[i];
+  int base = 0, m = 1, mc = 1;
+  for (int t = 0; t < h->n_inst(); ++t) {
+    Inst& x = h->inst[h->order[t]];
     make_spans(x.n_cells, x.ppc, target, &x.cps, &x.n_spans);
     x.span_base = base;
     base += x.n_spans;
     m = std::max(m, x.cps);
-    h->span_inst.insert(h->span_inst.end(), (size_t)x.n_spans, i);
+    mc = std::max(mc, x.n_cells);
+    h->span_inst.insert(h->span_inst.end(), (size_t)x.n_spans, t);
   }
   h->spans = base;
   h->max_cps = m;
+  h->max_cells = mc;
   h->tab_dirty = h->spans_dirty = true;
   h->graph_valid = false;
 }
 
-InstParams instance_params(const dsmc_sim* h, const Inst& x) {
+InstParams instance_params(const dsmc_sim* h, int id, int span_base) {
+  const Inst& x = h->inst[id];
   InstParams a{};
   a.n_cells = x.n_cells;
   a.cell_base = x.cell_base;
   a.off_base = x.off_base;
-  a.span_base = x.span_base;
+  a.span_base = span_base;
   a.n_spans = x.n_spans;
   a.cps = x.cps;
   a.part_base = x.part_base;
@@ -393,6 +490,8 @@ InstParams instance_params(const dsmc_sim* h, const Inst& x) {
   a.sample_start = h->opt.sample_start;
   a.collide = (h->opt.collisions != 0 && x.p.nsig > 0.0) ? 1 : 0;
   a.mode = collision_mode(x.omega);
+  a.id = id;
+  a.smax0 = x.p.smax0;
   return a;
 }
 
@@ -401,9 +500,10 @@ InstParams instance_params(const dsmc_sim* h, const Inst& x) {
 // pageable host memory, which CUDA stages before the call returns.
 dsmc_status upload_tables(dsmc_sim* h) {
   if (h->tab_dirty) {
-    h->tab.resize(h->inst.size());
-    for (int i = 0; i < h->n_inst(); ++i) h->tab[i] = instance_params(h, h->inst[i]);
-    if (h->n_inst() > 1)
+    h->tab.resize(h->order.size());
+    for (int t = 0; t < h->n_inst(); ++t)
+      h->tab[t] = instance_params(h, h->order[t], h->inst[h->order[t]].span_base);
+    if (!h->tab.empty())
       DSMC_CUDA(cudaMemcpyAsync(h->tab_dev, h->tab.data(), h->tab.size() * sizeof(InstParams),
                                 cudaMemcpyHostToDevice, h->stream()),
                 "instance table");
@@ -411,7 +511,7 @@ dsmc_status upload_tables(dsmc_sim* h) {
     if (h->n_inst() == 1) h->graph_valid = false;  // the captured launches hold tab[0]
   }
   if (h->spans_dirty) {
-    if (h->n_inst() > 1)
+    if (!h->span_inst.empty())
       DSMC_CUDA(cudaMemcpyAsync(h->span_inst_dev, h->span_inst.data(),
                                 h->span_inst.size() * sizeof(int), cudaMemcpyHostToDevice,
                                 h->stream()),
@@ -427,7 +527,7 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   L.tab = h->tab_dev;
   L.span_inst = h->span_inst_dev;
   L.n_spans_total = h->spans;
-  L.max_cells = h->L.max_cells;
+  L.max_cells = h->max_cells;
   L.max_cps = h->max_cps;
   L.max_cap = h->cap();
   L.gstep = h->gstep;
@@ -436,57 +536,123 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   return L;
 }
 
-// The launches of one pass over the records: collide + sample + move + count (or
-// count only), prefix over spans, cell offsets, stable scatter into the other buffer.
-dsmc_status run_pass(dsmc_sim* h, bool count_only) {
+// The launches of one pass over the records from buffer `src` to buffer src ^ 1:
+// collide + sample + move + count (or count only), prefix over spans, cell offsets,
+// stable scatter.
+dsmc_status launch_pass(dsmc_sim* h, bool count_only, const StepLaunch& SL,
+                        const InstParams& one, int src, int osrc) {
   cudaStream_t s = h->stream();
-  const StepLaunch SL = step_launch(h, count_only);
-  const InstParams& one = h->tab[0];
-  int* off_cur = h->off[h->ocur];
-  int* off_new = h->off[h->ocur ^ 1];
+  int* off_cur = h->off[osrc];
+  int* off_new = h->off[osrc ^ 1];
   DSMC_CUDA(timed(h, count_only ? K_INDEX_COUNT : K_COLLIDE_MOVE, [&] {
-              return launch_collide_move(h->P[h->cur], off_cur, h->smax[h->scur],
+              return launch_collide_move(h->P[src], off_cur, h->smax[h->scur],
                                          h->smax[h->scur ^ 1], h->ncand, h->nacc, h->acc,
                                          h->hist, one, SL, h->err, s);
             }),
             count_only ? "index_count" : "collide_move");
-  if (!count_only) h->scur ^= 1;
   DSMC_CUDA(timed(h, K_SCAN, [&] { return launch_scan_spans(h->hist, h->count, one, SL, s); }),
             "scan_hist");
   DSMC_CUDA(timed(h, K_OFFSETS,
                   [&] { return launch_offsets_cells(h->count, off_new, one, SL, s); }),
             "cell_offsets");
   DSMC_CUDA(timed(h, count_only ? K_INDEX_SCATTER : K_SCATTER_SPANS, [&] {
-              return launch_scatter_spans(h->P[h->cur], h->P[h->cur ^ 1], off_cur, off_new,
-                                          h->hist, one, SL, h->err, s);
+              return launch_scatter_spans(h->P[src], h->P[src ^ 1], off_cur, off_new, h->hist,
+                                          one, SL, h->err, s);
             }),
             count_only ? "index_scatter" : "scatter_spans");
+  return DSMC_OK;
+}
+
+// One pass over every active instance from the current buffers to the other ones.
+dsmc_status run_pass(dsmc_sim* h, bool count_only) {
+  if (h->n_inst() == 0) return DSMC_OK;
+  const StepLaunch SL = step_launch(h, count_only);
+  dsmc_status s = launch_pass(h, count_only, SL, h->tab[0], h->cur, h->ocur);
+  if (s != DSMC_OK) return s;
+  if (!count_only) h->scur ^= 1;
   h->cur ^= 1;
   h->ocur ^= 1;
   return DSMC_OK;
 }
 
-// Sort into cells without moving (creation, state load).  The current offsets must
-// describe slot ranges per cell span; records may be in any order within them.
+// Sort into cells without moving (state load).  The current offsets must describe
+// slot ranges per cell span; records may be in any order within them.
 dsmc_status run_index(dsmc_sim* h) {
   dsmc_status s = upload_tables(h);
   if (s != DSMC_OK) return s;
   return run_pass(h, /*count_only=*/true);
 }
 
-// Advances every instance's counters for one step.
+// Device initialisation of the instances added since the last step: particles drawn
+// into the idle record buffer with offsets of whole cells, per-cell arrays reset, then
+// a sort into cells of those instances alone into the current buffers (the other
+// instances are not touched).
+dsmc_status admit_fresh(dsmc_sim* h) {
+  std::vector<int> ids;
+  for (int id : h->order)
+    if (h->inst[id].fresh) ids.push_back(id);
+  if (ids.empty()) return DSMC_OK;
+  cudaStream_t s = h->stream();
+  const int idle = h->cur ^ 1, oidle = h->ocur ^ 1;
+  h->adm_tab.clear();
+  h->adm_span.clear();
+  int base = 0, m = 1, mc = 1;
+  for (size_t k = 0; k < ids.size(); ++k) {
+    const Inst& x = h->inst[ids[k]];
+    h->adm_tab.push_back(instance_params(h, ids[k], base));
+    h->adm_span.insert(h->adm_span.end(), (size_t)x.n_spans, (int)k);
+    base += x.n_spans;
+    m = std::max(m, x.cps);
+    mc = std::max(mc, x.n_cells);
+    DSMC_CUDA(timed(h, K_INIT, [&] {
+                return launch_init(h->P[idle] + x.part_base, (int)x.N, x.ppc, (float)x.n_cells,
+                                   (uint32_t)(x.seed & 0xffffffffu), (uint32_t)(x.seed >> 32),
+                                   h->err, s);
+              }),
+              "init");
+  }
+  InstParams* adm_tab_dev = h->tab_dev + h->C.inst;
+  int* adm_span_dev = h->span_inst_dev + h->C.spans;
+  DSMC_CUDA(cudaMemcpyAsync(adm_tab_dev, h->adm_tab.data(), h->adm_tab.size() * sizeof(InstParams),
+                            cudaMemcpyHostToDevice, s),
+            "admission table");
+  DSMC_CUDA(cudaMemcpyAsync(adm_span_dev, h->adm_span.data(), h->adm_span.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s),
+            "admission span table");
+  DSMC_CUDA(launch_admit_cells(adm_tab_dev, (int)ids.size(), h->off[oidle], h->smax[h->scur],
+                               h->ncand, h->nacc, h->acc, s),
+            "admit cells");
+  StepLaunch SL{};
+  SL.n_inst = (int)ids.size();
+  SL.tab = adm_tab_dev;
+  SL.span_inst = adm_span_dev;
+  SL.n_spans_total = base;
+  SL.max_cells = mc;
+  SL.max_cps = m;
+  SL.max_cap = h->cap();
+  SL.gstep = h->gstep;
+  SL.gstep_dev = nullptr;
+  SL.count_only = 1;
+  dsmc_status st = launch_pass(h, true, SL, h->adm_tab[0], idle, oidle);
+  if (st != DSMC_OK) return st;
+  for (int id : ids) h->inst[id].fresh = false;
+  return DSMC_OK;
+}
+
+// Advances every active instance's counters for one step.
 void count_step(dsmc_sim* h) {
   h->gstep += 1;
-  for (Inst& x : h->inst) {
+  for (int id : h->order) {
+    Inst& x = h->inst[id];
     x.step += 1;
     if (x.step >= h->opt.sample_start) x.n_samples += 1;
   }
 }
 
-// Slot ranges for a sort of instance i's records in arbitrary order: cell span k
+// Slot ranges for a sort of instance id's records in arbitrary order: cell span k
 // covers [off[k cps], off[(k+1) cps]) with off[c] = part_base + floor(c N / n_cells).
-dsmc_status set_uniform_offsets(dsmc_sim* h, int i, std::vector<int>& host) {
-  const Inst& x = h->inst[i];
+dsmc_status set_uniform_offsets(dsmc_sim* h, int id, std::vector<int>& host) {
+  const Inst& x = h->inst[id];
   host.resize((size_t)x.n_cells + 1);
   for (int c = 0; c <= x.n_cells; ++c)
     host[c] = x.part_base + (int)((long long)c * x.N / x.n_cells);
@@ -520,10 +686,11 @@ dsmc_status check_handle(dsmc_sim* h) {
   return DSMC_OK;
 }
 
-dsmc_status check_index(dsmc_sim* h, int i) {
+dsmc_status check_index(dsmc_sim* h, int id) {
   dsmc_status s = check_handle(h);
   if (s != DSMC_OK) return s;
-  if (i < 0 || i >= h->n_inst()) return fail(DSMC_E_INVAL, "instance index out of range");
+  if (id < 0 || id >= (int)h->inst.size() || !h->inst[id].active)
+    return fail(DSMC_E_INVAL, "instance index out of range or not active");
   return DSMC_OK;
 }
 
@@ -574,8 +741,9 @@ dsmc_status step_once(dsmc_sim* h) {
 
 dsmc_status step_n(dsmc_sim* h, int n_steps) {
   dsmc_status s;
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
   int it = 0;
-  if (h->opt.graph && !h->opt.profile) {
+  if (h->opt.graph && !h->opt.profile && h->n_inst() > 0) {
     while (n_steps - it >= kGraphSteps) {
       if ((s = upload_tables(h)) != DSMC_OK) return s;
       if (!h->graph_valid || h->graph_parity != parity(h))
@@ -592,50 +760,83 @@ dsmc_status step_n(dsmc_sim* h, int n_steps) {
   return DSMC_OK;
 }
 
-dsmc_status create_run(const dsmc_instance* defs, int n_inst, const dsmc_options* opt_in,
-                       void* workspace, size_t workspace_bytes, dsmc_handle* out) {
-  if (!out) return fail(DSMC_E_INVAL, "out: NULL");
-  *out = nullptr;
-  if (!defs) return fail(DSMC_E_INVAL, "instances: NULL");
-  if (n_inst < 1 || n_inst > kMaxInstances)
-    return fail(DSMC_E_INVAL, "n_instances must be 1..65535");
-  dsmc_options opt;
-  dsmc_default_options(&opt);
-  if (opt_in) opt = *opt_in;
-  dsmc_status st = check_options(&opt);
+// Adds an instance (extents, parameters, counters); its device data is set up by the
+// next step or synchronising call.  *id gets its id.
+dsmc_status add_instance(dsmc_sim* h, const dsmc_instance& d, int index, int n_def, int* id) {
+  dsmc_status st = check_instance(d, index, n_def);
   if (st != DSMC_OK) return st;
-  std::vector<Inst> v((size_t)n_inst);
-  long long slots = 0;
-  for (int i = 0; i < n_inst; ++i) {
-    const dsmc_instance& d = defs[i];
-    if ((st = check_instance(d, i, n_inst)) != DSMC_OK) return st;
-    Inst& x = v[i];
-    x.omega = d.gas.omega;
-    x.Kn = d.Kn;
-    x.wall_T = d.wall_T;
-    x.F = d.body_force;
-    x.n_cells = d.n_cells;
-    x.ppc = d.ppc;
-    x.N = (long long)d.n_cells * d.ppc;
-    x.seed = d.seed;
-    if (!derive_params(x.omega, x.Kn, x.F, x.ppc, opt, &x.p))
-      return fail(DSMC_E_INVAL, (n_inst > 1 ? "instance " + std::to_string(i) + ": " : "") +
-                                    "time step undefined: set options.dt for infinite Kn");
-    slots += (x.N + 63) & ~63LL;
+  Inst x;
+  x.omega = d.gas.omega;
+  x.Kn = d.Kn;
+  x.wall_T = d.wall_T;
+  x.F = d.body_force;
+  x.n_cells = d.n_cells;
+  x.ppc = d.ppc;
+  x.N = (long long)d.n_cells * d.ppc;
+  x.seed = d.seed;
+  if (!derive_params(x.omega, x.Kn, x.F, x.ppc, h->opt, &x.p))
+    return fail(DSMC_E_INVAL, (n_def > 1 ? "instance " + std::to_string(index) + ": " : "") +
+                                  "time step undefined: set options.dt for infinite Kn");
+  int mcps, mcells;
+  partition_extent(h, h->span_target, &x, &mcps, &mcells);
+  if (!step_fits(mcells, mcps, h->opt.group_size))
+    return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
+  // Find a free id and room in every array.
+  int new_id = -1;
+  for (int i = 0; i < (int)h->inst.size(); ++i)
+    if (!h->inst[i].active) {
+      new_id = i;
+      break;
+    }
+  if (new_id < 0 && (int)h->inst.size() >= h->C.inst)
+    return fail(DSMC_E_NOMEM, "no room: instance table full");
+  x.max_spans = reserved_spans(x.n_cells, x.ppc);
+  if (h->spans_reserved + x.max_spans > h->C.spans)
+    return fail(DSMC_E_NOMEM, "no room: span table full");
+  x.slot_len = padded_slots(x.N);
+  const long long ps = h->ex_slots.alloc(x.slot_len);
+  const long long cb = ps < 0 ? -1 : h->ex_cells.alloc(x.n_cells);
+  const long long ob = cb < 0 ? -1 : h->ex_offs.alloc(x.n_cells + 1);
+  const long long hb = ob < 0 ? -1 : h->ex_hist.alloc((long long)x.max_spans * x.n_cells);
+  if (hb < 0) {
+    if (ob >= 0) h->ex_offs.release(ob, x.n_cells + 1);
+    if (cb >= 0) h->ex_cells.release(cb, x.n_cells);
+    if (ps >= 0) h->ex_slots.release(ps, x.slot_len);
+    return fail(DSMC_E_NOMEM, "no room: device memory of the handle is taken");
   }
-  if (slots > kMaxParticles)
-    return fail(DSMC_E_INVAL, "the instances' particles (each padded to 64) must total <= 2^31 - 2^24");
+  x.part_base = (int)ps;
+  x.cell_base = (int)cb;
+  x.off_base = (int)ob;
+  x.hist_base = hb;
+  x.active = true;
+  x.fresh = true;
+  if (new_id < 0) {
+    new_id = (int)h->inst.size();
+    h->inst.push_back(x);
+  } else {
+    h->inst[new_id] = x;
+  }
+  h->order.push_back(new_id);
+  h->spans_reserved += x.max_spans;
+  set_partition(h, h->span_target);
+  *id = new_id;
+  return DSMC_OK;
+}
 
+// Allocates the handle and its device workspace for capacity C.
+dsmc_status new_handle(const Capacity& C, const dsmc_options& opt, bool pool, void* workspace,
+                       size_t workspace_bytes, dsmc_sim** out) {
   dsmc_sim* h = new (std::nothrow) dsmc_sim();
   if (!h) return fail(DSMC_E_NOMEM, "host allocation failed");
-  h->inst = std::move(v);
+  h->pool = pool;
   h->opt = opt;
-  h->L = place(h->inst);
-  set_partition(h, opt.span_particles ? opt.span_particles : kDefaultSpanParticles);
-  if (!step_fits(h->L.max_cells, h->max_cps, opt.group_size)) {
-    delete h;
-    return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
-  }
+  h->C = C;
+  h->L = layout_of(C);
+  h->span_target = opt.span_particles ? opt.span_particles : kDefaultSpanParticles;
+  h->ex_slots.reset(C.slots);
+  h->ex_cells.reset(C.cells);
+  h->ex_offs.reset(C.offs);
+  h->ex_hist.reset(C.hist_ints);
   cudaError_t ce = cudaGetDevice(&h->device);
   if (ce != cudaSuccess) {
     delete h;
@@ -660,62 +861,92 @@ dsmc_status create_run(const dsmc_instance* defs, int n_inst, const dsmc_options
   const Layout& L = h->L;
   char* b = (char*)h->ws;
   h->P[0] = (float4*)(b + L.st);
-  h->P[1] = h->P[0] + L.n_slots;
+  h->P[1] = h->P[0] + C.slots;
   h->hist = (int*)(b + L.hist);
   h->count = (int*)(b + L.count);
   h->off[0] = (int*)(b + L.offset);
-  h->off[1] = h->off[0] + L.offs;
+  h->off[1] = h->off[0] + C.offs;
   h->smax[0] = (float*)(b + L.smax);
-  h->smax[1] = h->smax[0] + L.cells;
+  h->smax[1] = h->smax[0] + C.cells;
   h->ncand = (unsigned long long*)(b + L.ncand);
   h->nacc = (unsigned long long*)(b + L.nacc);
   h->acc = (double*)(b + L.acc);
   h->tab_dev = (InstParams*)(b + L.tab);
   h->span_inst_dev = (int*)(b + L.span_inst);
+  h->chan_dev = (double*)(b + L.chan);
   h->err = (int*)(b + L.err);
   h->gstep_dev = (long long*)(b + L.err + 8);
-
-  auto bail = [&](dsmc_status s) {
+  ce = set_step_smem_limits(kStepSmemMax, kStepSmemMax);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream());
+  if (ce != cudaSuccess) {
+    dsmc_status s = cuda_fail(ce, "handle setup");
     dsmc_destroy(h);
     return s;
-  };
-  cudaStream_t s = h->stream();
-  ce = set_step_smem_limits(kStepSmemMax, kStepSmemMax);
-  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaFuncSetAttribute"));
-  const size_t nc = (size_t)L.cells;
-  if ((ce = cudaMemsetAsync(h->acc, 0, nc * kNMom * sizeof(double), s)) != cudaSuccess ||
-      (ce = cudaMemsetAsync(h->ncand, 0, nc * 8, s)) != cudaSuccess ||
-      (ce = cudaMemsetAsync(h->nacc, 0, nc * 8, s)) != cudaSuccess ||
-      (ce = cudaMemsetAsync(h->err, 0, sizeof(int), s)) != cudaSuccess)
-    return bail(cuda_fail(ce, "cudaMemsetAsync"));
-  // Initial (sigma g)_max per cell and slot ranges of whole cells (particle p of an
-  // instance is drawn in its cell p / ppc).
-  std::vector<float> smax0(nc);
-  std::vector<int> off0((size_t)L.offs);
-  for (const Inst& x : h->inst) {
-    std::fill(smax0.begin() + x.cell_base, smax0.begin() + x.cell_base + x.n_cells, x.p.smax0);
-    for (int c = 0; c <= x.n_cells; ++c) off0[(size_t)x.off_base + c] = x.part_base + c * x.ppc;
   }
-  ce = cudaMemcpyAsync(h->smax[0], smax0.data(), nc * sizeof(float), cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(h->off[h->ocur], off0.data(), off0.size() * sizeof(int),
-                         cudaMemcpyHostToDevice, s);
-  if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMemcpyAsync"));
-  for (const Inst& x : h->inst) {
-    ce = timed(h, K_INIT, [&] {
-      return launch_init(h->P[0] + x.part_base, (int)x.N, x.ppc, (float)x.n_cells,
-                         (uint32_t)(x.seed & 0xffffffffu), (uint32_t)(x.seed >> 32), h->err, s);
-    });
-    if (ce != cudaSuccess) return bail(cuda_fail(ce, "init"));
-  }
-  st = run_index(h);
-  if (st != DSMC_OK) return bail(st);
-  ce = cudaStreamSynchronize(s);  // the host buffers must outlive their copies
-  if (ce != cudaSuccess) return bail(cuda_fail(ce, "stream sync"));
+  *out = h;
+  return DSMC_OK;
+}
+
+// Sets up fresh instances on the device and checks for errors (synchronises).
+dsmc_status settle(dsmc_sim* h) {
+  dsmc_status st = admit_fresh(h);
+  if (st != DSMC_OK) return st;
   st = collect_times(h);
-  if (st != DSMC_OK) return bail(st);
-  st = read_error_word(h);
-  if (st != DSMC_OK) return bail(st);
+  if (st != DSMC_OK) return st;
+  return read_error_word(h);
+}
+
+dsmc_status create_run(const dsmc_instance* defs, int n_inst, const dsmc_options* opt_in,
+                       void* workspace, size_t workspace_bytes, dsmc_handle* out) {
+  if (!out) return fail(DSMC_E_INVAL, "out: NULL");
+  *out = nullptr;
+  if (!defs) return fail(DSMC_E_INVAL, "instances: NULL");
+  if (n_inst < 1 || n_inst > kMaxInstances)
+    return fail(DSMC_E_INVAL, "n_instances must be 1..65535");
+  dsmc_options opt;
+  dsmc_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  dsmc_status st = check_options(&opt);
+  if (st != DSMC_OK) return st;
+  for (int i = 0; i < n_inst; ++i)
+    if ((st = check_instance(defs[i], i, n_inst)) != DSMC_OK) return st;
+  long long slots = 0;
+  for (int i = 0; i < n_inst; ++i) slots += padded_slots((long long)defs[i].n_cells * defs[i].ppc);
+  if (slots > kMaxParticles)
+    return fail(DSMC_E_INVAL, "the instances' particles (each padded to 64) must total <= 2^31 - 2^24");
+  // Parameters and shared-memory fit before any device work.
+  {
+    int mcps = 1, mcells = 1;
+    const int target = opt.span_particles ? opt.span_particles : kDefaultSpanParticles;
+    for (int i = 0; i < n_inst; ++i) {
+      Params p;
+      if (!derive_params(defs[i].gas.omega, defs[i].Kn, defs[i].body_force, defs[i].ppc, opt, &p))
+        return fail(DSMC_E_INVAL, (n_inst > 1 ? "instance " + std::to_string(i) + ": " : "") +
+                                      "time step undefined: set options.dt for infinite Kn");
+      int cps, ns;
+      make_spans(defs[i].n_cells, defs[i].ppc, target, &cps, &ns);
+      mcps = std::max(mcps, cps);
+      mcells = std::max(mcells, defs[i].n_cells);
+    }
+    if (!step_fits(mcells, mcps, opt.group_size))
+      return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
+  }
+  dsmc_sim* h = nullptr;
+  st = new_handle(capacity_of(defs, n_inst), opt, false, workspace, workspace_bytes, &h);
+  if (st != DSMC_OK) return st;
+  for (int i = 0; i < n_inst; ++i) {
+    int id = -1;
+    st = add_instance(h, defs[i], i, n_inst, &id);
+    if (st != DSMC_OK) {
+      dsmc_destroy(h);
+      return st;
+    }
+  }
+  st = settle(h);
+  if (st != DSMC_OK) {
+    dsmc_destroy(h);
+    return st;
+  }
   *out = h;
   return DSMC_OK;
 }
@@ -754,14 +985,9 @@ dsmc_status dsmc_default_options(dsmc_options* opt) {
 
 size_t dsmc_batch_workspace_bytes(const dsmc_instance* inst, int n_inst) {
   if (!inst || n_inst < 1 || n_inst > kMaxInstances) return 0;
-  std::vector<Inst> v((size_t)n_inst);
-  for (int i = 0; i < n_inst; ++i) {
+  for (int i = 0; i < n_inst; ++i)
     if (inst[i].n_cells < 1 || inst[i].ppc < 1 || inst[i].n_cells > kMaxStepCells) return 0;
-    v[i].n_cells = inst[i].n_cells;
-    v[i].ppc = inst[i].ppc;
-    v[i].N = (long long)inst[i].n_cells * inst[i].ppc;
-  }
-  return place(v).total;
+  return layout_of(capacity_of(inst, n_inst)).total;
 }
 
 size_t dsmc_workspace_bytes(int n_cells, int ppc) {
@@ -769,6 +995,16 @@ size_t dsmc_workspace_bytes(int n_cells, int ppc) {
   d.n_cells = n_cells;
   d.ppc = ppc;
   return dsmc_batch_workspace_bytes(&d, 1);
+}
+
+size_t dsmc_pool_workspace_bytes(const dsmc_pool_limits* limits) {
+  Capacity C;
+  const std::string saved = g_last_error;
+  if (capacity_of_pool(limits, &C) != DSMC_OK) {
+    g_last_error = saved;
+    return 0;
+  }
+  return layout_of(C).total;
 }
 
 dsmc_status dsmc_create_in(const dsmc_gas* gas, double Kn, double wall_T, double body_force,
@@ -792,7 +1028,77 @@ dsmc_status dsmc_create_batch(const dsmc_instance* inst, int n_inst, const dsmc_
   return create_run(inst, n_inst, opt, workspace, workspace_bytes, out);
 }
 
+dsmc_status dsmc_pool_create(const dsmc_pool_limits* limits, const dsmc_options* opt_in,
+                             void* workspace, size_t workspace_bytes, dsmc_handle* out) {
+  if (!out) return fail(DSMC_E_INVAL, "out: NULL");
+  *out = nullptr;
+  Capacity C;
+  dsmc_status st = capacity_of_pool(limits, &C);
+  if (st != DSMC_OK) return st;
+  dsmc_options opt;
+  dsmc_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if ((st = check_options(&opt)) != DSMC_OK) return st;
+  dsmc_sim* h = nullptr;
+  st = new_handle(C, opt, true, workspace, workspace_bytes, &h);
+  if (st != DSMC_OK) return st;
+  *out = h;
+  return DSMC_OK;
+}
+
+dsmc_status dsmc_pool_add(dsmc_handle h, const dsmc_instance* inst, int* id) {
+  dsmc_status s = check_handle(h);
+  if (s != DSMC_OK) return s;
+  if (!inst || !id) return fail(DSMC_E_INVAL, "instance and id must not be NULL");
+  if (!h->pool) return fail(DSMC_E_STATE, "dsmc_pool_add needs a handle from dsmc_pool_create");
+  *id = -1;
+  return add_instance(h, *inst, 0, 1, id);
+}
+
+dsmc_status dsmc_pool_remove(dsmc_handle h, int id) {
+  dsmc_status s = check_index(h, id);
+  if (s != DSMC_OK) return s;
+  if (!h->pool) return fail(DSMC_E_STATE, "dsmc_pool_remove needs a handle from dsmc_pool_create");
+  Inst& x = h->inst[id];
+  // Work already enqueued on the stream still reads these ranges; anything that reuses
+  // them is enqueued after it.
+  h->ex_slots.release(x.part_base, x.slot_len);
+  h->ex_cells.release(x.cell_base, x.n_cells);
+  h->ex_offs.release(x.off_base, x.n_cells + 1);
+  h->ex_hist.release(x.hist_base, (long long)x.max_spans * x.n_cells);
+  h->spans_reserved -= x.max_spans;
+  x.active = false;
+  x.fresh = false;
+  h->order.erase(std::find(h->order.begin(), h->order.end(), id));
+  set_partition(h, h->span_target);
+  return DSMC_OK;
+}
+
+dsmc_status dsmc_channel_sums(dsmc_handle h, double* out) {
+  dsmc_status s = check_handle(h);
+  if (s != DSMC_OK) return s;
+  if (!out) return fail(DSMC_E_INVAL, "out: NULL");
+  DeviceGuard guard(h->device);
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
+  if ((s = upload_tables(h)) != DSMC_OK) return s;
+  const size_t n_ids = h->inst.size();
+  if (h->n_inst() > 0)
+    DSMC_CUDA(launch_channel_sums(h->tab_dev, h->n_inst(), h->acc, h->chan_dev, h->stream()),
+              "channel sums");
+  if (n_ids > 0)
+    DSMC_CUDA(cudaMemcpyAsync(out, h->chan_dev, 2 * n_ids * sizeof(double), cudaMemcpyDefault,
+                              h->stream()),
+              "copy channel sums");
+  s = dsmc_sync(h);
+  if (s != DSMC_OK) return s;
+  for (size_t i = 0; i < n_ids; ++i)
+    if (!h->inst[i].active) out[2 * i] = out[2 * i + 1] = 0.0;
+  return DSMC_OK;
+}
+
 int dsmc_batch_size(dsmc_handle h) { return h ? h->n_inst() : 0; }
+
+int dsmc_id_bound(dsmc_handle h) { return h ? (int)h->inst.size() : 0; }
 
 dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt) {
   dsmc_status s = check_handle(h);
@@ -800,21 +1106,23 @@ dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt) {
   s = check_options(opt);
   if (s != DSMC_OK) return s;
   std::vector<Params> ps(h->inst.size());
-  for (int i = 0; i < h->n_inst(); ++i) {
-    const Inst& x = h->inst[i];
-    if (!derive_params(x.omega, x.Kn, x.F, x.ppc, *opt, &ps[i]))
+  for (int id : h->order) {
+    const Inst& x = h->inst[id];
+    if (!derive_params(x.omega, x.Kn, x.F, x.ppc, *opt, &ps[id]))
       return fail(DSMC_E_INVAL, "time step undefined: set options.dt for infinite Kn");
   }
   // span_particles = 0 keeps the partition in use (default or tuned).
   const int target_use = opt->span_particles ? opt->span_particles : h->span_target;
-  if (!step_fits(h->L.max_cells, partition_max_cps(h, target_use), opt->group_size))
+  int mcps, mcells;
+  partition_extent(h, target_use, nullptr, &mcps, &mcells);
+  if (!step_fits(mcells, mcps, opt->group_size))
     return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   if (h->events_used) {
     s = collect_times(h);
     if (s != DSMC_OK) return s;
   }
   h->opt = *opt;
-  for (int i = 0; i < h->n_inst(); ++i) h->inst[i].p = ps[i];
+  for (int id : h->order) h->inst[id].p = ps[id];
   if (target_use != h->span_target) set_partition(h, target_use);
   h->tab_dirty = true;
   drop_graph(h);  // launch shapes or the stream may have changed
@@ -839,6 +1147,7 @@ dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_par
   if (s != DSMC_OK) return s;
   if (steps_per_trial < 1) return fail(DSMC_E_INVAL, "steps_per_trial must be >= 1");
   if (h->latched != DSMC_OK) return fail(h->latched, "an earlier step reached a device limit");
+  if (h->n_inst() == 0) return fail(DSMC_E_STATE, "no instances to tune on");
   DeviceGuard guard(h->device);
   cudaStream_t st = h->stream();
   cudaEvent_t e0, e1;
@@ -849,20 +1158,21 @@ dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_par
   }
   int best = h->span_target;
   double best_ms = -1.0;
-  int last_cps = -1;
+  long long last_sig = -1;
   dsmc_status r = DSMC_OK;
   for (int target = kMinSpanParticles; target <= (1 << 17) && r == DSMC_OK; target *= 2) {
-    const int mc = partition_max_cps(h, target);
-    if (!step_fits(h->L.max_cells, mc, h->opt.group_size)) break;
+    int mcps, mcells;
+    partition_extent(h, target, nullptr, &mcps, &mcells);
+    if (!step_fits(mcells, mcps, h->opt.group_size)) break;
     // Skip targets that give the same partition as the last one.
-    int sig = 0;
-    for (const Inst& x : h->inst) {
+    long long sig = 0;
+    for (int id : h->order) {
       int cps, ns;
-      make_spans(x.n_cells, x.ppc, target, &cps, &ns);
-      sig = sig * 31 + cps;
+      make_spans(h->inst[id].n_cells, h->inst[id].ppc, target, &cps, &ns);
+      sig = (sig * 1000003 + cps) & 0x3fffffffffffLL;
     }
-    if (sig == last_cps) continue;
-    last_cps = sig;
+    if (sig == last_sig) continue;
+    last_sig = sig;
     set_partition(h, target);
     // one untimed step with the new partition, then the timed trial
     if ((r = step_n(h, 1)) != DSMC_OK) break;
@@ -893,17 +1203,16 @@ dsmc_status dsmc_sync(dsmc_handle h) {
   dsmc_status s = check_handle(h);
   if (s != DSMC_OK) return s;
   DeviceGuard guard(h->device);
-  s = collect_times(h);
-  if (s != DSMC_OK) return s;
-  return read_error_word(h);
+  return settle(h);
 }
 
-dsmc_status dsmc_sample_moments_of(dsmc_handle h, int i, double* out, long long* n_samples) {
-  dsmc_status s = check_index(h, i);
+dsmc_status dsmc_sample_moments_of(dsmc_handle h, int id, double* out, long long* n_samples) {
+  dsmc_status s = check_index(h, id);
   if (s != DSMC_OK) return s;
   if (!out) return fail(DSMC_E_INVAL, "out: NULL");
   DeviceGuard guard(h->device);
-  const Inst& x = h->inst[i];
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
+  const Inst& x = h->inst[id];
   DSMC_CUDA(cudaMemcpyAsync(out, h->acc + (size_t)x.cell_base * kNMom,
                             (size_t)x.n_cells * kNMom * sizeof(double), cudaMemcpyDefault,
                             h->stream()),
@@ -921,20 +1230,23 @@ dsmc_status dsmc_sample_moments_all(dsmc_handle h, double* out, long long* n_sam
   if (s != DSMC_OK) return s;
   if (!out) return fail(DSMC_E_INVAL, "out: NULL");
   DeviceGuard guard(h->device);
-  DSMC_CUDA(cudaMemcpyAsync(out, h->acc, (size_t)h->L.cells * kNMom * sizeof(double),
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
+  DSMC_CUDA(cudaMemcpyAsync(out, h->acc, (size_t)h->C.cells * kNMom * sizeof(double),
                             cudaMemcpyDefault, h->stream()),
             "copy moments");
   if (n_samples)
-    for (int i = 0; i < h->n_inst(); ++i) n_samples[i] = h->inst[i].n_samples;
+    for (size_t i = 0; i < h->inst.size(); ++i)
+      n_samples[i] = h->inst[i].active ? h->inst[i].n_samples : 0;
   return dsmc_sync(h);
 }
 
-dsmc_status dsmc_reset_samples_of(dsmc_handle h, int i) {
-  dsmc_status s = check_index(h, i);
+dsmc_status dsmc_reset_samples_of(dsmc_handle h, int id) {
+  dsmc_status s = check_index(h, id);
   if (s != DSMC_OK) return s;
   DeviceGuard guard(h->device);
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
   cudaStream_t st = h->stream();
-  Inst& x = h->inst[i];
+  Inst& x = h->inst[id];
   const size_t c0 = (size_t)x.cell_base, nc = (size_t)x.n_cells;
   DSMC_CUDA(cudaMemsetAsync(h->acc + c0 * kNMom, 0, nc * kNMom * sizeof(double), st), "reset");
   DSMC_CUDA(cudaMemsetAsync(h->ncand + c0, 0, nc * 8, st), "reset");
@@ -946,23 +1258,19 @@ dsmc_status dsmc_reset_samples_of(dsmc_handle h, int i) {
 dsmc_status dsmc_reset_samples(dsmc_handle h) {
   dsmc_status s = check_handle(h);
   if (s != DSMC_OK) return s;
-  DeviceGuard guard(h->device);
-  cudaStream_t st = h->stream();
-  const size_t nc = (size_t)h->L.cells;
-  DSMC_CUDA(cudaMemsetAsync(h->acc, 0, nc * kNMom * sizeof(double), st), "reset");
-  DSMC_CUDA(cudaMemsetAsync(h->ncand, 0, nc * 8, st), "reset");
-  DSMC_CUDA(cudaMemsetAsync(h->nacc, 0, nc * 8, st), "reset");
-  for (Inst& x : h->inst) x.n_samples = 0;
+  for (int id : h->order)
+    if ((s = dsmc_reset_samples_of(h, id)) != DSMC_OK) return s;
   return DSMC_OK;
 }
 
-dsmc_status dsmc_copy_state_of(dsmc_handle h, int i, float* y, float* vx, float* vy,
+dsmc_status dsmc_copy_state_of(dsmc_handle h, int id, float* y, float* vx, float* vy,
                                float* vz) {
-  dsmc_status s = check_index(h, i);
+  dsmc_status s = check_index(h, id);
   if (s != DSMC_OK) return s;
   DeviceGuard guard(h->device);
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
   cudaStream_t st = h->stream();
-  const Inst& x = h->inst[i];
+  const Inst& x = h->inst[id];
   // Unpack the records into four arrays in the instance's part of the idle sort
   // buffer, then copy out.
   float* tmp = reinterpret_cast<float*>(h->P[h->cur ^ 1] + x.part_base);
@@ -983,13 +1291,14 @@ dsmc_status dsmc_copy_state(dsmc_handle h, float* y, float* vx, float* vy, float
   return dsmc_copy_state_of(h, 0, y, vx, vy, vz);
 }
 
-dsmc_status dsmc_copy_cells_of(dsmc_handle h, int i, int* offset, float* smax,
+dsmc_status dsmc_copy_cells_of(dsmc_handle h, int id, int* offset, float* smax,
                                unsigned long long* ncand, unsigned long long* nacc) {
-  dsmc_status s = check_index(h, i);
+  dsmc_status s = check_index(h, id);
   if (s != DSMC_OK) return s;
   DeviceGuard guard(h->device);
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
   cudaStream_t st = h->stream();
-  const Inst& x = h->inst[i];
+  const Inst& x = h->inst[id];
   const size_t c0 = (size_t)x.cell_base, nc = (size_t)x.n_cells;
   if (offset) {
     // Offsets relative to the instance's first slot (as for a run of its own).
@@ -1019,16 +1328,17 @@ dsmc_status dsmc_copy_cells(dsmc_handle h, int* offset, float* smax, unsigned lo
   return dsmc_copy_cells_of(h, 0, offset, smax, ncand, nacc);
 }
 
-dsmc_status dsmc_load_state_of(dsmc_handle h, int i, const float* y, const float* vx,
+dsmc_status dsmc_load_state_of(dsmc_handle h, int id, const float* y, const float* vx,
                                const float* vy, const float* vz, const float* smax,
                                long long step) {
-  dsmc_status s = check_index(h, i);
+  dsmc_status s = check_index(h, id);
   if (s != DSMC_OK) return s;
   if (!y || !vx || !vy || !vz) return fail(DSMC_E_INVAL, "state arrays must not be NULL");
   if (step < 0) return fail(DSMC_E_INVAL, "step must be >= 0");
   DeviceGuard guard(h->device);
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
   cudaStream_t st = h->stream();
-  Inst& x = h->inst[i];
+  Inst& x = h->inst[id];
   float* tmp = reinterpret_cast<float*>(h->P[h->cur ^ 1] + x.part_base);
   const size_t n = (size_t)x.N;
   const float* src[4] = {y, vx, vy, vz};
@@ -1045,7 +1355,7 @@ dsmc_status dsmc_load_state_of(dsmc_handle h, int i, const float* y, const float
   x.step = step;
   h->tab_dirty = true;
   std::vector<int> host;
-  s = set_uniform_offsets(h, i, host);
+  s = set_uniform_offsets(h, id, host);
   if (s != DSMC_OK) return s;
   // The sort pass runs over every instance: for the others, already in cell order,
   // the stable sort leaves records and offsets unchanged.
@@ -1059,11 +1369,11 @@ dsmc_status dsmc_load_state(dsmc_handle h, const float* y, const float* vx, cons
   return dsmc_load_state_of(h, 0, y, vx, vy, vz, smax, step);
 }
 
-dsmc_status dsmc_get_info_of(dsmc_handle h, int i, dsmc_info* info) {
-  dsmc_status s = check_index(h, i);
+dsmc_status dsmc_get_info_of(dsmc_handle h, int id, dsmc_info* info) {
+  dsmc_status s = check_index(h, id);
   if (s != DSMC_OK) return s;
   if (!info) return fail(DSMC_E_INVAL, "info: NULL");
-  const Inst& x = h->inst[i];
+  const Inst& x = h->inst[id];
   info->n_particles = x.N;
   info->n_cells = x.n_cells;
   info->ppc = x.ppc;
@@ -1089,6 +1399,7 @@ dsmc_status dsmc_get_info_of(dsmc_handle h, int i, dsmc_info* info) {
   info->n_spans = x.n_spans;
   info->total_spans = h->spans;
   info->first_slot = x.part_base;
+  info->first_cell = x.cell_base;
   return DSMC_OK;
 }
 

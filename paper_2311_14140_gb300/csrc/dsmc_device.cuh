@@ -230,9 +230,10 @@ __device__ __forceinline__ int group_count(int nc, int G) {
 
 // Free flight of one particle over dt with the body force along x and fully
 // diffuse walls at the wall temperature.  Returns false at the bounce limit.
-__device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, float dt,
-                                    float F, uint32_t k0, uint32_t k1, uint32_t step,
-                                    uint32_t slot) {
+// `gen(c0, c1, c2, c3)` is the Philox4x32-10 generator of the run's key.
+template <class Gen>
+__device__ __forceinline__ bool fly_with(float& y, float& vx, float& vy, float& vz, float dt,
+                                         float F, uint32_t step, uint32_t slot, Gen gen) {
   float t = dt;
   bool ok = true;
   for (int b = 0;; ++b) {
@@ -257,12 +258,12 @@ __device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, f
     t = fsub(t, thit);
     const uint32_t c1 = (uint32_t)b << 8;
     const uint32_t c3 = kStreamMove << 24;
-    U4 w = philox(slot, c1, step, c3, k0, k1);
+    U4 w = gen(slot, c1, step, c3);
     const float speed = fsqrt(-ln32(u01(w.x)));
     float z0 = 0.0f, z1 = 0.0f;
     bool got = false;
     for (int a = 0; a < kNormalAttempts && !got; ++a) {
-      if ((a & 1) == 0) w = philox(slot, c1 | (1u + (uint32_t)(a >> 1)), step, c3, k0, k1);
+      if ((a & 1) == 0) w = gen(slot, c1 | (1u + (uint32_t)(a >> 1)), step, c3);
       got = (a & 1) ? polar_pair(w.z, w.w, z0, z1) : polar_pair(w.x, w.y, z0, z1);
     }
     if (!got) {
@@ -275,6 +276,25 @@ __device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, f
     vy = (wall == 0.0f) ? speed : -speed;
     y = wall;
   }
+}
+
+__device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, float dt,
+                                    float F, uint32_t k0, uint32_t k1, uint32_t step,
+                                    uint32_t slot) {
+  return fly_with(y, vx, vy, vz, dt, F, step, slot,
+                  [=](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+                    return philox(a, b, c, d, k0, k1);
+                  });
+}
+
+// The same with the key's round keys precomputed.
+__device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, float dt,
+                                    float F, const PhiloxKeys& rk, uint32_t step,
+                                    uint32_t slot) {
+  return fly_with(y, vx, vy, vz, dt, F, step, slot,
+                  [&](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+                    return philox_rk(a, b, c, d, rk);
+                  });
 }
 
 }  // namespace dsmc

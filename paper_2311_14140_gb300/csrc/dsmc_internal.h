@@ -91,7 +91,9 @@ struct InstParams {
   long long step0;         // the instance's step k runs at global step step0 + k
   long long sample_start;  // instance steps >= sample_start are sampled
   int collide;
-  int mode;  // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
+  int mode;     // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
+  int id;       // the instance's id in its handle
+  float smax0;  // initial (sigma g)_max / sigma_ref of every cell
 };
 
 // Dynamic shared memory of one collide/move CTA (byte offsets).
@@ -178,6 +180,16 @@ cudaError_t launch_scan_spans(int* hist, int* count, const InstParams& one, cons
 cudaError_t launch_offsets_cells(const int* count, int* off_new, const InstParams& one,
                                  const StepLaunch& L, cudaStream_t st);
 cudaError_t launch_set_counter(long long* counter, long long value, cudaStream_t st);
+// Per-cell arrays of newly added instances (table `tab`, n of them): moment sums and
+// collision counters zeroed, (sigma g)_max set to smax0, and cell offsets of whole
+// cells of ppc = n_part / n_cells particles starting at part_base.
+cudaError_t launch_admit_cells(const InstParams* tab, int n, int* off, float* smax,
+                               unsigned long long* ncand, unsigned long long* nacc,
+                               double* acc, cudaStream_t st);
+// Per instance of `tab` (n of them): the sums over its cells of the sampled particle
+// count and of vx, into out[2 id] and out[2 id + 1].
+cudaError_t launch_channel_sums(const InstParams* tab, int n, const double* acc, double* out,
+                                cudaStream_t st);
 cudaError_t launch_unpack(const float4* P, float* y, float* vx, float* vy, float* vz, int N,
                           cudaStream_t st);
 cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const float* vz,

@@ -258,14 +258,24 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
     caccn[i] = 0;
     cgmax[i] = 0u;
   }
-  if (threadIdx.x == 0) {
-    int q = 0;
-    for (int c = c0; c < c1; ++c) {
-      gfirst[c - c0] = q;
-      q += group_count(off[c + 1] - off[c], G);
+  if (wib == 0) {  // group prefix over the span's cells, 32 cells at a time
+    int base = 0;
+    for (int i0 = 0; i0 < c1 - c0; i0 += 32) {
+      const int i = i0 + lane;
+      const int g = (i < c1 - c0) ? group_count(off[c0 + i + 1] - off[c0 + i], G) : 0;
+      int incl = g;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (i < c1 - c0) gfirst[i] = base + incl - g;
+      base += __shfl_sync(kFull, incl, 31);
     }
-    gfirst[c1 - c0] = q;
-    *next_group = 0;
+    if (lane == 0) {
+      gfirst[c1 - c0] = base;
+      *next_group = 0;
+    }
   }
   for (int i = lane; i < cap; i += 32) touch[i] = 0u;
   if (lane == 0) {
@@ -463,7 +473,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
         const int p = gs + i;
         const float4 r = rec[i];
         float yy = r.x, xx = r.y, uy = r.z, zz = r.w;
-        if (!fly(yy, xx, uy, zz, a.dt, a.F, a.k0, a.k1, step, (uint32_t)(p - a.part_base)))
+        if (!fly(yy, xx, uy, zz, a.dt, a.F, a.keys, step, (uint32_t)(p - a.part_base)))
           bad_bounce = true;
         P[p] = make_float4(yy, xx, uy, zz);
         atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
@@ -683,6 +693,57 @@ __global__ void __launch_bounds__(1024)
 
 __global__ void k_set_counter(long long* counter, long long value) { *counter = value; }
 
+__global__ void __launch_bounds__(256)
+    k_admit_cells(const InstParams* __restrict__ tab, int* __restrict__ off_all,
+                  float* __restrict__ smax_all, unsigned long long* __restrict__ ncand_all,
+                  unsigned long long* __restrict__ nacc_all, double* __restrict__ acc_all) {
+  const InstParams& a = tab[blockIdx.x];
+  const int n_cells = a.n_cells;
+  const int ppc = a.n_part / n_cells;
+  int* off = off_all + a.off_base;
+  for (int c = threadIdx.x; c <= n_cells; c += blockDim.x) off[c] = a.part_base + c * ppc;
+  for (int c = threadIdx.x; c < n_cells; c += blockDim.x) {
+    smax_all[a.cell_base + c] = a.smax0;
+    ncand_all[a.cell_base + c] = 0ull;
+    nacc_all[a.cell_base + c] = 0ull;
+  }
+  double* acc = acc_all + (size_t)a.cell_base * kNMom;
+  for (int i = threadIdx.x; i < n_cells * kNMom; i += blockDim.x) acc[i] = 0.0;
+}
+
+__global__ void __launch_bounds__(256)
+    k_channel_sums(const InstParams* __restrict__ tab, const double* __restrict__ acc_all,
+                   double* __restrict__ out) {
+  __shared__ double part[2][8];
+  const InstParams& a = tab[blockIdx.x];
+  const double* acc = acc_all + (size_t)a.cell_base * kNMom;
+  double n = 0.0, u = 0.0;
+  for (int c = threadIdx.x; c < a.n_cells; c += blockDim.x) {
+    n += acc[(size_t)c * kNMom + 0];
+    u += acc[(size_t)c * kNMom + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    part[0][w] = n;
+    part[1][w] = u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sn = 0.0, su = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      sn += part[0][k];
+      su += part[1][k];
+    }
+    out[2 * a.id] = sn;
+    out[2 * a.id + 1] = su;
+  }
+}
+
 // Records <-> four arrays (y, vx, vy, vz), for the state accessors.
 __global__ void k_unpack(const float4* __restrict__ P, float* __restrict__ y,
                          float* __restrict__ vx, float* __restrict__ vy, float* __restrict__ vz,
@@ -767,6 +828,19 @@ cudaError_t launch_offsets_cells(const int* count, int* off_new, const InstParam
 
 cudaError_t launch_set_counter(long long* counter, long long value, cudaStream_t st) {
   k_set_counter<<<1, 1, 0, st>>>(counter, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_admit_cells(const InstParams* tab, int n, int* off, float* smax,
+                               unsigned long long* ncand, unsigned long long* nacc,
+                               double* acc, cudaStream_t st) {
+  k_admit_cells<<<n, 256, 0, st>>>(tab, off, smax, ncand, nacc, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_channel_sums(const InstParams* tab, int n, const double* acc, double* out,
+                                cudaStream_t st) {
+  k_channel_sums<<<n, 256, 0, st>>>(tab, acc, out);
   return cudaGetLastError();
 }
 

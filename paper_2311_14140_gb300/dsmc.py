@@ -54,13 +54,36 @@ class Info(ctypes.Structure):
                 ("smax0", ctypes.c_float), ("device_bytes", ctypes.c_size_t),
                 ("n_instances", ctypes.c_int), ("span_particles", ctypes.c_int),
                 ("cells_per_span", ctypes.c_int), ("n_spans", ctypes.c_int),
-                ("total_spans", ctypes.c_int), ("first_slot", ctypes.c_int)]
+                ("total_spans", ctypes.c_int), ("first_slot", ctypes.c_int),
+                ("first_cell", ctypes.c_int)]
 
 
 class Instance(ctypes.Structure):
     _fields_ = [("gas", Gas), ("Kn", ctypes.c_double), ("wall_T", ctypes.c_double),
                 ("body_force", ctypes.c_double), ("n_cells", ctypes.c_int),
                 ("ppc", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class PoolLimits(ctypes.Structure):
+    _fields_ = [("max_particles", ctypes.c_longlong), ("max_cells", ctypes.c_int),
+                ("max_instances", ctypes.c_int), ("max_cells_per_instance", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("instance", Instance), ("arrival", ctypes.c_double),
+                ("target_se", ctypes.c_double), ("max_steps", ctypes.c_longlong)]
+
+
+class ServeOptions(ctypes.Structure):
+    _fields_ = [("epoch_steps", ctypes.c_int), ("batches", ctypes.c_int),
+                ("max_active", ctypes.c_int), ("time_limit", ctypes.c_double)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_double), ("finished", ctypes.c_double),
+                ("steps", ctypes.c_longlong), ("u_mean", ctypes.c_double),
+                ("u_se", ctypes.c_double), ("count", ctypes.c_double),
+                ("sum_vx", ctypes.c_double), ("converged", ctypes.c_int), ("id", ctypes.c_int)]
 
 
 _lib = None
@@ -110,6 +133,18 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsmc_get_info_of": (st, [H, c.c_int, c.POINTER(Info)]),
         "dsmc_autotune": (st, [H, c.c_int, c.POINTER(c.c_int), c.POINTER(c.c_double)]),
         "dsmc_sort_cells_static": (st, [c.c_void_p] * 9 + [c.c_int, c.c_int, c.c_void_p]),
+        "dsmc_id_bound": (c.c_int, [H]),
+        "dsmc_channel_sums": (st, [H, c.c_void_p]),
+        "dsmc_pool_workspace_bytes": (c.c_size_t, [c.POINTER(PoolLimits)]),
+        "dsmc_pool_create": (st, [c.POINTER(PoolLimits), c.POINTER(Options), c.c_void_p,
+                                  c.c_size_t, c.POINTER(H)]),
+        "dsmc_pool_add": (st, [H, c.POINTER(Instance), c.POINTER(c.c_int)]),
+        "dsmc_pool_remove": (st, [H, c.c_int]),
+        "dsmc_default_serve_options": (st, [c.POINTER(ServeOptions)]),
+        "dsmc_serve": (st, [H, c.POINTER(Request), c.c_int, c.POINTER(ServeOptions),
+                            c.POINTER(RequestResult)]),
+        "dsmc_solve": (st, [c.POINTER(Request), c.POINTER(Options), c.POINTER(ServeOptions),
+                            c.POINTER(RequestResult)]),
         "dsmc_kernel_count": (c.c_int, []),
         "dsmc_kernel_name": (c.c_char_p, [c.c_int]),
         "dsmc_kernel_times": (st, [H, c.c_void_p, c.c_void_p]),
@@ -296,51 +331,36 @@ def make_instance(Kn: float, n_cells: int, ppc: int, *, omega: float = 0.5,
                     int(seed) & 0xFFFFFFFFFFFFFFFF)
 
 
-class DsmcBatch:
-    """Many independent DSMC runs advanced by the same launches (``dsmc_create_batch``).
+def _options(dt_factor=0.2, dt=0.0, sample_start=0, group_size=256, collisions=True,
+             profile=False, span_particles=0, graph=False) -> Options:
+    o = default_options()
+    o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
+    o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
+    o.span_particles, o.graph = int(span_particles), int(bool(graph))
+    return o
 
-    ``instances``: a sequence of dicts with the keyword arguments of ``make_instance``
-    (Kn, n_cells, ppc, omega, body_force, seed, wall_T).  Options are shared.  Instance
-    i evolves exactly as ``Dsmc(**instances[i], ...)`` with the same options.
-    """
 
-    def __init__(self, instances, *, dt_factor: float = 0.2, dt: float = 0.0,
-                 sample_start: int = 0, group_size: int = 256, collisions: bool = True,
-                 profile: bool = False, span_particles: int = 0, graph: bool = False,
-                 stream=None, workspace: str = "torch"):
-        L = load_library()
-        self._lib = L
-        self._defs = [dict(d) for d in instances]
-        arr = (Instance * len(self._defs))(*[make_instance(**d) for d in self._defs])
-        self._arr = arr
-        self.n = len(self._defs)
-        self.n_cells = [int(d["n_cells"]) for d in self._defs]
-        self.ppc = [int(d["ppc"]) for d in self._defs]
-        self.cell_base = np.concatenate([[0], np.cumsum(self.n_cells)]).astype(np.int64)
-        o = default_options()
-        o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
-        o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
-        o.span_particles, o.graph = int(span_particles), int(bool(graph))
-        self._ws = None
+class _Multi:
+    """Accessors of a handle with several instances, by instance id."""
+
+    _lib = None
+    _h = None
+    _opt = None
+    _ws = None
+
+    def _alloc(self, workspace: str, nbytes: int, stream):
+        """(workspace pointer, bytes, stream) for a torch-owned or library-owned handle."""
         if workspace == "torch":
             import torch
-            nbytes = L.dsmc_batch_workspace_bytes(arr, self.n)
             if nbytes == 0:
-                raise DsmcError(1, "invalid instance sizes")
+                raise DsmcError(1, "invalid sizes")
             self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
             if stream is None:
                 stream = torch.cuda.current_stream().cuda_stream
-            ws_ptr, ws_bytes = self._ws.data_ptr(), nbytes
-        elif workspace == "library":
-            ws_ptr, ws_bytes = None, 0
-        else:
-            raise ValueError("workspace must be 'torch' or 'library'")
-        o.stream = int(stream) if stream is not None else None
-        self._opt = o
-        h = ctypes.c_void_p()
-        _check(L.dsmc_create_batch(arr, self.n, ctypes.byref(o), ws_ptr, ws_bytes,
-                                   ctypes.byref(h)))
-        self._h = h
+            return self._ws.data_ptr(), nbytes, stream
+        if workspace == "library":
+            return None, 0, stream
+        raise ValueError("workspace must be 'torch' or 'library'")
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -383,21 +403,21 @@ class DsmcBatch:
         self._opt.span_particles = best.value
         return best.value, ms.value
 
+    def size(self) -> int:
+        return self._lib.dsmc_batch_size(self._h)
+
     def moments(self, i: int, out=None):
         if out is None:
-            out = np.empty((self.n_cells[i], NMOM), np.float64)
+            out = np.empty((self.info(i)["n_cells"], NMOM), np.float64)
         ns = ctypes.c_longlong()
         _check(self._lib.dsmc_sample_moments_of(self._h, int(i), _ptr(out), ctypes.byref(ns)))
         return out, int(ns.value)
 
-    def moments_all(self, out=None):
-        """(raw sums [sum n_cells, 13], sampled steps per instance); rows of instance i
-        are ``cell_base[i]:cell_base[i+1]``."""
-        if out is None:
-            out = np.empty((int(self.cell_base[-1]), NMOM), np.float64)
-        ns = np.empty(self.n, np.int64)
-        _check(self._lib.dsmc_sample_moments_all(self._h, _ptr(out), _ptr(ns)))
-        return out, ns
+    def channel_sums(self):
+        """[id bound, 2]: sampled particle count and sum of vx per instance id."""
+        out = np.zeros((max(1, self._lib.dsmc_id_bound(self._h)), 2), np.float64)
+        _check(self._lib.dsmc_channel_sums(self._h, _ptr(out)))
+        return out
 
     def reset_samples(self, i: Optional[int] = None) -> None:
         if i is None:
@@ -406,13 +426,13 @@ class DsmcBatch:
             _check(self._lib.dsmc_reset_samples_of(self._h, int(i)))
 
     def state(self, i: int):
-        n = self.n_cells[i] * self.ppc[i]
+        n = self.info(i)["n_particles"]
         arrs = [np.empty(n, np.float32) for _ in range(4)]
         _check(self._lib.dsmc_copy_state_of(self._h, int(i), *[_ptr(a) for a in arrs]))
         return tuple(arrs)
 
     def cells(self, i: int):
-        nc = self.n_cells[i]
+        nc = self.info(i)["n_cells"]
         off = np.empty(nc + 1, np.int32)
         smax = np.empty(nc, np.float32)
         cand = np.empty(nc, np.uint64)
@@ -443,6 +463,115 @@ class DsmcBatch:
 
     def reset_kernel_times(self) -> None:
         _check(self._lib.dsmc_reset_kernel_times(self._h))
+
+
+class DsmcBatch(_Multi):
+    """Many independent DSMC runs advanced by the same launches (``dsmc_create_batch``).
+
+    ``instances``: a sequence of dicts with the keyword arguments of ``make_instance``
+    (Kn, n_cells, ppc, omega, body_force, seed, wall_T).  Options are shared.  Instance
+    i evolves exactly as ``Dsmc(**instances[i], ...)`` with the same options.
+    """
+
+    def __init__(self, instances, *, stream=None, workspace: str = "torch", **opts):
+        L = load_library()
+        self._lib = L
+        self._defs = [dict(d) for d in instances]
+        arr = (Instance * len(self._defs))(*[make_instance(**d) for d in self._defs])
+        self.n = len(self._defs)
+        self.n_cells = [int(d["n_cells"]) for d in self._defs]
+        self.ppc = [int(d["ppc"]) for d in self._defs]
+        self.cell_base = np.concatenate([[0], np.cumsum(self.n_cells)]).astype(np.int64)
+        o = _options(**opts)
+        ws_ptr, ws_bytes, stream = self._alloc(
+            workspace, L.dsmc_batch_workspace_bytes(arr, self.n) if workspace == "torch" else 0,
+            stream)
+        o.stream = int(stream) if stream is not None else None
+        self._opt = o
+        h = ctypes.c_void_p()
+        _check(L.dsmc_create_batch(arr, self.n, ctypes.byref(o), ws_ptr, ws_bytes,
+                                   ctypes.byref(h)))
+        self._h = h
+
+    def moments_all(self, out=None):
+        """(raw sums [sum n_cells, 13], sampled steps per instance); rows of instance i
+        are ``cell_base[i]:cell_base[i+1]``."""
+        if out is None:
+            out = np.empty((int(self.cell_base[-1]), NMOM), np.float64)
+        ns = np.empty(self.n, np.int64)
+        _check(self._lib.dsmc_sample_moments_all(self._h, _ptr(out), _ptr(ns)))
+        return out, ns
+
+
+class DsmcPool(_Multi):
+    """A handle whose instances come and go (``dsmc_pool_create``): continuous batching."""
+
+    def __init__(self, max_particles: int, max_cells: int, max_instances: int,
+                 max_cells_per_instance: int, *, stream=None, workspace: str = "torch",
+                 **opts):
+        L = load_library()
+        self._lib = L
+        self.limits = PoolLimits(int(max_particles), int(max_cells), int(max_instances),
+                                 int(max_cells_per_instance))
+        o = _options(**opts)
+        ws_ptr, ws_bytes, stream = self._alloc(
+            workspace,
+            L.dsmc_pool_workspace_bytes(ctypes.byref(self.limits)) if workspace == "torch" else 0,
+            stream)
+        o.stream = int(stream) if stream is not None else None
+        self._opt = o
+        h = ctypes.c_void_p()
+        _check(L.dsmc_pool_create(ctypes.byref(self.limits), ctypes.byref(o), ws_ptr, ws_bytes,
+                                  ctypes.byref(h)))
+        self._h = h
+
+    def add(self, **instance) -> int:
+        """Adds a run (keyword arguments of ``make_instance``); returns its id.  Raises
+        DsmcError (status 2) when the pool has no room."""
+        inst = make_instance(**instance)
+        i = ctypes.c_int(-1)
+        _check(self._lib.dsmc_pool_add(self._h, ctypes.byref(inst), ctypes.byref(i)))
+        return i.value
+
+    def remove(self, i: int) -> None:
+        _check(self._lib.dsmc_pool_remove(self._h, int(i)))
+
+    def serve(self, requests, *, epoch_steps: int = 32, batches: int = 16, max_active: int = 0,
+              time_limit: float = 0.0):
+        """Runs ``dsmc_serve`` over ``requests`` (a sequence of dicts with ``arrival``,
+        ``target_se``, ``max_steps`` and the keyword arguments of ``make_instance``);
+        returns one dict per request."""
+        arr = (Request * len(requests))()
+        for k, r in enumerate(requests):
+            inst = {x: r[x] for x in r if x not in ("arrival", "target_se", "max_steps")}
+            arr[k] = Request(make_instance(**inst), float(r["arrival"]), float(r["target_se"]),
+                             int(r["max_steps"]))
+        so = serve_options(epoch_steps=epoch_steps, batches=batches, max_active=max_active,
+                           time_limit=time_limit)
+        res = (RequestResult * len(requests))()
+        _check(self._lib.dsmc_serve(self._h, arr, len(requests), ctypes.byref(so), res))
+        return [{k: getattr(x, k) for k, _ in RequestResult._fields_} for x in res]
+
+
+def serve_options(**kw) -> ServeOptions:
+    so = ServeOptions()
+    _check(load_library().dsmc_default_serve_options(ctypes.byref(so)))
+    for k, v in kw.items():
+        setattr(so, k, v)
+    return so
+
+
+def solve(request: dict, *, epoch_steps: int = 32, batches: int = 16, **opts) -> dict:
+    """One request as a plain run of its own (``dsmc_solve``)."""
+    inst = {x: request[x] for x in request if x not in ("arrival", "target_se", "max_steps")}
+    r = Request(make_instance(**inst), float(request.get("arrival", 0.0)),
+                float(request["target_se"]), int(request["max_steps"]))
+    o = _options(**opts)
+    so = serve_options(epoch_steps=epoch_steps, batches=batches)
+    res = RequestResult()
+    _check(load_library().dsmc_solve(ctypes.byref(r), ctypes.byref(o), ctypes.byref(so),
+                                      ctypes.byref(res)))
+    return {k: getattr(res, k) for k, _ in RequestResult._fields_}
 
 
 def fields(acc, n_samples: int, ppc: int) -> dict:

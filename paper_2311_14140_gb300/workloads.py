@@ -83,3 +83,21 @@ def batch_instances(n: int = 256, seed: int = 12345):
                             steps=2000, sample_start=1001,
                             seeds=(int(rng.integers(0, 2 ** 63 - 1)),)))
     return out
+
+
+def serving_requests(n: int = 2000, rate: float = 50.0, target_se: float = 0.01,
+                     max_steps: int = 200_000, seed: int = 4242):
+    """Micro-solve requests: Poisson arrivals at `rate` per second (exponential gaps),
+    each a run drawn as in batch_instances (Kn log-uniform in [0.05, 10], 50-1000
+    cells, 50-400 particles per cell, force 0.5-2 x f0_force(1), hard spheres, own
+    seed), to a relative standard error `target_se` of the channel-mean velocity."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    t -= t[0]
+    out = []
+    for i, w in enumerate(batch_instances(n, seed=seed + 1)):
+        out.append(dict(Kn=w.Kn, n_cells=w.n_cells, ppc=w.ppc, omega=w.omega,
+                        body_force=w.body_force, seed=w.seeds[0], arrival=float(t[i]),
+                        target_se=float(target_se), max_steps=int(max_steps)))
+    return out

@@ -127,6 +127,68 @@ def test_batch_workspace_is_the_sum_of_its_parts(lib):
     assert lib.dsmc_batch_size(None) == 0
 
 
+def test_binding_structs_match_the_header(tmp_path):
+    """sizeof and every field offset of the header's structs, as a C compiler lays them
+    out, equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    structs = {"dsmc_gas": D.Gas, "dsmc_options": D.Options, "dsmc_info": D.Info,
+               "dsmc_instance": D.Instance, "dsmc_pool_limits": D.PoolLimits,
+               "dsmc_request": D.Request, "dsmc_serve_options": D.ServeOptions,
+               "dsmc_request_result": D.RequestResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dsmc.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(x.split()[:2]): int(x.split()[2]) for x in out if x}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_pool_limits_are_checked(lib):
+    bad = [D.PoolLimits(0, 10, 4, 10), D.PoolLimits(1 << 20, 10, 0, 10),
+           D.PoolLimits(1 << 20, 10, 4, 20), D.PoolLimits(1 << 20, 100000, 4, 20000)]
+    for lim in bad:
+        assert lib.dsmc_pool_workspace_bytes(ctypes.byref(lim)) == 0
+        h = ctypes.c_void_p()
+        assert lib.dsmc_pool_create(ctypes.byref(lim), None, None, 0, ctypes.byref(h)) == 1
+    ok = D.PoolLimits(1 << 20, 10000, 64, 1000)
+    assert lib.dsmc_pool_workspace_bytes(ctypes.byref(ok)) >= 32 * (1 << 20)
+    i = ctypes.c_int()
+    inst = D.make_instance(Kn=1.0, n_cells=10, ppc=10)
+    assert lib.dsmc_pool_add(None, ctypes.byref(inst), ctypes.byref(i)) == 1
+    assert lib.dsmc_pool_remove(None, 0) == 1
+    assert lib.dsmc_channel_sums(None, None) == 1
+
+
+def test_serve_arguments_are_checked(lib):
+    so = D.serve_options()
+    assert (so.epoch_steps, so.batches, so.max_active, so.time_limit) == (32, 16, 0, 0.0)
+    inst = D.make_instance(Kn=1.0, n_cells=10, ppc=10)
+    res = (D.RequestResult * 2)()
+    reqs = (D.Request * 2)(D.Request(inst, 1.0, 0.01, 100), D.Request(inst, 0.5, 0.01, 100))
+    # a NULL pool, then requests out of order, then bad targets: all rejected on the host
+    assert lib.dsmc_serve(None, reqs, 2, ctypes.byref(so), res) == 1
+    r1 = (D.Request * 1)(D.Request(inst, 0.0, 0.0, 100))
+    assert lib.dsmc_solve(r1, None, ctypes.byref(so), res) == 1
+    assert "target_se" in lib.dsmc_last_error().decode()
+    bad = D.serve_options(batches=1)
+    r2 = (D.Request * 1)(D.Request(inst, 0.0, 0.01, 100))
+    assert lib.dsmc_solve(r2, None, ctypes.byref(bad), res) == 1
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.dsmc_step(None, 1) == 1
     assert lib.dsmc_sync(None) == 1
