@@ -7,10 +7,10 @@
  * The problem (Sec. 2.1): a monatomic gas between two plates held at a constant
  * temperature, driven by an external acceleration F parallel to the plates, in
  * steady, fully developed, one-dimensional flow.  Everything is nondimensional as in
- * Eq. 5: lengths in the plate gap H (walls at y = 0 and y = 1), speeds in
+ * Eq. 6: lengths in the plate gap H (walls at y = 0 and y = 1), speeds in
  * v0 = sqrt(2 k T0 / m) with T0 the wall temperature, time in H / v0, body force
  * in v0^2 / H, stress in P0.  The Knudsen number enters through the viscosity,
- * mu0 v0 / (P0 H) = 2 Kn / sqrt(pi) (Eq. 7 against Eq. 3).  The DSMC method itself
+ * mu0 v0 / (P0 H) = 2 Kn / sqrt(pi) (Eq. 7 against Eq. 2).  The DSMC method itself
  * is Bird's, which the paper cites (Sec. 1, Sec. 2) without describing it.
  *
  * One time step (a call to dsmc_step advances n of them), in this order:
@@ -154,7 +154,7 @@ DSMC_API size_t dsmc_workspace_bytes(int n_cells, int ppc);
  * cell with velocity components N(0, 1/2) (the gas at rest at the wall
  * temperature, Sec. 2.1), then sorted into cells.  Kn > 0 (+INFINITY: collisionless,
  * then options.dt must be set); wall_T > 0 is the reference temperature T0;
- * body_force is F = F' H / v0^2 (Eq. 5); 1 <= n_cells <= 16384, ppc >= 1,
+ * body_force is F = F' H / v0^2 (Eq. 6); 1 <= n_cells <= 16384, ppc >= 1,
  * n_cells * ppc <= 2^31 - 2^24 (with group_size 512 and more than ~12,000 cells the
  * step's shared memory may not fit: DSMC_E_INVAL).  The library allocates the device memory.  Initialisation
  * is enqueued on the legacy default stream and completed before return. */

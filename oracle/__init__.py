@@ -278,7 +278,7 @@ class OracleSim:
 def fields(acc: np.ndarray, n_samples: int, ppc: int) -> dict:
     """Cell fields from the raw moment sums of ``OracleSim.moments`` (plain numpy).
 
-    Units as in Eq. 5 of the paper: density relative to the initial one, velocity in
+    Units as in Eq. 6 of the paper: density relative to the initial one, velocity in
     v0, temperature in T0, shear stress P_xy in P0 = n0 k T0 (rho / P0 = 2 / v0^2),
     heat flux in P0 v0.
     """

@@ -14,9 +14,9 @@
  *   - the problem: monatomic gas between two plates at a constant temperature, driven
  *     by a small external acceleration parallel to the plates (Sec. 2.1);
  *   - the nondimensionalisation: lengths in H, speeds in v0 = sqrt(2 k T0 / m), body
- *     force F = F' H / v0^2, stress in P0 (Eq. 5);
+ *     force F = F' H / v0^2, stress in P0 (Eq. 6);
  *   - the Knudsen number through the viscosity, mu0 v0 / (P0 H) = 2 Kn / sqrt(pi)
- *     (Eq. 7 against Eq. 3);
+ *     (Eq. 7 against Eq. 2);
  *   - the DSMC cell size and particles per cell as free inputs, and sampling by time
  *     averaging (Sec. 3);
  *   - the DSMC method itself, which the paper takes from Bird (cited in Sec. 1 and
@@ -206,7 +206,7 @@ OR_EXPORT float or_pow(float g, float a) {
 
 /* One attempt of the Marsaglia-Bray polar method: two words -> two independent
  * N(0, 1/2) deviates, or a rejection (returns 0).  The variance 1/2 is the
- * Maxwellian at the wall temperature in v0 units (Eq. 5). */
+ * Maxwellian at the wall temperature in v0 units (Eq. 6). */
 OR_EXPORT int or_normal_pair(uint32_t w0, uint32_t w1, float* z0, float* z1) {
   float a0 = 2.0f * or_u01(w0) - 1.0f;
   float a1 = 2.0f * or_u01(w1) - 1.0f;
@@ -259,7 +259,7 @@ static int family_normals(const family* f, float* z, int n) {
 /* Simulation parameters (host arithmetic in binary64, rounded once to binary32). */
 
 /* Number density times reference cross-section, in 1/H, from the viscosity
- * definition of Kn: mu0 v0 / (P0 H) = 2 Kn / sqrt(pi) (Eq. 7 with Eq. 3) and the
+ * definition of Kn: mu0 v0 / (P0 H) = 2 Kn / sqrt(pi) (Eq. 7 with Eq. 2) and the
  * first Chapman-Enskog viscosity of VHS molecules,
  *   mu = 15 sqrt(pi m k T) / (2 sigma (5 - 2w)(7 - 2w))      (Bird),
  * which together give n sigma H = 15 sqrt(2) pi / (4 (5-2w)(7-2w) Kn).

@@ -4,7 +4,7 @@
 //
 //   k_init            initial state: ppc particles per cell, uniform in the cell,
 //                     velocity components N(0, 1/2) (gas at rest at the wall
-//                     temperature, Sec. 2.1, units of Eq. 5)
+//                     temperature, Sec. 2.1, units of Eq. 6)
 //   k_move_count      (optional free flight,) new cell, warp-private histogram over
 //                     fixed spans of slots: the sort into cells at creation, after a
 //                     state load, and in the allocation-free sort

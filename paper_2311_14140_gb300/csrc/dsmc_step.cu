@@ -1,5 +1,5 @@
 // dsmc_step.cu -- the two state passes of one DSMC step (Bird's method, which the
-// paper cites for its micro model; problem of Sec. 2.1, units of Eq. 5).
+// paper cites for its micro model; problem of Sec. 2.1, units of Eq. 6).
 //
 // The resident particle state is an array of float4 records (y, vx, vy, vz): one
 // 16-byte load or store moves a whole particle, so the sort's scattered writes cost

@@ -576,7 +576,7 @@ def solve(request: dict, *, epoch_steps: int = 32, batches: int = 16, **opts) ->
 
 def fields(acc, n_samples: int, ppc: int) -> dict:
     """Cell fields from raw sums: relative density n, velocity (v0), temperature (T0),
-    shear stress P_xy (P0; rho / P0 = 2 / v0^2 in the units of Eq. 5) and heat flux
+    shear stress P_xy (P0; rho / P0 = 2 / v0^2 in the units of Eq. 6) and heat flux
     (P0 v0), from central moments of the sampled velocities."""
     a = np.asarray(acc, np.float64)
     cnt = a[:, 0]

@@ -11,7 +11,7 @@ code; these tests check the oracle against what kinetic theory and the paper fix
 * free-molecular transient: without collisions, u(y, t) = F E[min(t, tau(y, vy))] over
   vy ~ N(0, 1/2), tau the time since the particle left a wall (1D quadrature);
 * momentum balance: the steady shear stress obeys dP_xy/dy = 2F at every Kn (Eq. 1 in
-  the units of Eq. 5, rho / P0 = 2 / v0^2);
+  the units of Eq. 6, rho / P0 = 2 / v0^2);
 * near-continuum limit: at Kn = 0.05 the interior velocity is the parabola of Eq. 8
   with S = 0, curvature -sqrt(pi) F / Kn, up to the exact hard-sphere viscosity being
   1.016 times the first Chapman-Enskog value the Kn definition (Eq. 7) uses; the wall

@@ -4,7 +4,7 @@ Each check compares the oracle with something other than itself: cuRAND's host
 Philox4_32_10 generator (a library that runs on the CPU), the published Philox
 known-answer vectors, binary64 libm, and the distributions the DSMC method needs
 (N(0,1/2) velocity components of a Maxwellian at the wall temperature in v0 units,
-Eq. 5 of the paper, and the flux-weighted half-Maxwellian of a diffuse wall).
+Eq. 6 of the paper, and the flux-weighted half-Maxwellian of a diffuse wall).
 """
 import ctypes
 import math
