@@ -350,6 +350,77 @@ DSMC_API dsmc_status dsmc_serve(dsmc_handle pool, const dsmc_request* requests, 
 DSMC_API dsmc_status dsmc_solve(const dsmc_request* request, const dsmc_options* opt,
                                 const dsmc_serve_options* so, dsmc_request_result* result);
 
+/* The device address of instance i's moment sums (n_cells x DSMC_NMOM binary64, the
+ * layout of dsmc_sample_moments), valid until the handle is destroyed or the instance
+ * removed; its contents change with every step.  For consumers on the device. */
+DSMC_API dsmc_status dsmc_device_moments_of(dsmc_handle h, int i, const double** acc);
+
+/* The surrogate stage (Sec. 2.3, Appendix A): training samples from windows of DSMC
+ * moment sums, Bayesian ridge regression with evidence maximisation for the boundary
+ * models (no-slip Eq. 11, first-order slip Eq. 12) and the constitutive models C0..C3
+ * (Eq. 13 with the stress correction Eq. 14 and Table 1 exponents), selection by
+ * Eq. 17 with equal priors, and the corrected macroscopic solve (Eq. 8 with Eqs. 9-10)
+ * with Monte Carlo uncertainty bands from the posteriors.  All arithmetic binary64.
+ *
+ * A training sample is one window of sampled steps of a run with n_cells cells of
+ * ppc particles: per cell u = sum vx / N and P_xy = 2 n (<vx vy> - <vx><vy>),
+ * n = N / (steps ppc); the constitutive targets are E_i = P_i + (2 Kn / sqrt(pi)) du/dy
+ * at the cells with two neighbours (central differences), the boundary targets the
+ * wall velocities extrapolated linearly from the two nearest cells, with
+ * P^CFD(wall) = F (2y - 1) = -F, +F.  The regression has no intercept and flat
+ * hyperpriors; a weight precision above 1e30 switches the weights off. */
+typedef struct dsmc_surrogate* dsmc_surrogate_handle;
+
+typedef struct dsmc_surrogate_fit {
+  long long n_samples;      /* training samples (windows) */
+  double n_v, n_c;          /* data points of the boundary and constitutive models */
+  double log_evidence_v[2]; /* no-slip, slip */
+  double prob_v[2];
+  double alpha_v[2], beta_v[2];
+  double sigma_p, sigma_p_var; /* slip coefficient: posterior mean and variance */
+  int iterations_v;
+  double log_evidence_c[4]; /* C0..C3 */
+  double prob_c[4];
+  double alpha_c[4], beta_c[4];
+  double m_c[4][3];         /* posterior means a_1..a_k of C_k */
+  double S_c[4][9];         /* posterior covariances (k x k block of a row-major 3x3) */
+  int iterations_c[4];
+  int sel_v, sel_c;         /* selected models: 0 no-slip / 1 slip; k of C_k */
+  double b[3];              /* exponents used */
+} dsmc_surrogate_fit;
+
+/* Table 1 exponents at the tabulated Kn nearest in log Kn (b[3]). */
+DSMC_API dsmc_status dsmc_surrogate_exponents(double Kn, double* b);
+
+/* A surrogate for runs of n_cells (>= 3) cells with ppc particles per cell at Kn with
+ * body force F != 0; b = NULL takes Table 1.  Device work goes on `stream`. */
+DSMC_API dsmc_status dsmc_surrogate_create(double Kn, double F, int n_cells, int ppc,
+                                           const double* b, void* stream,
+                                           dsmc_surrogate_handle* out);
+DSMC_API dsmc_status dsmc_surrogate_destroy(dsmc_surrogate_handle s);
+/* Forget all training samples. */
+DSMC_API dsmc_status dsmc_surrogate_reset(dsmc_surrogate_handle s);
+/* One training sample from a window's raw sums (n_cells x DSMC_NMOM, host or device)
+ * of n_steps sampled steps. */
+DSMC_API dsmc_status dsmc_surrogate_add_window(dsmc_surrogate_handle s, const double* acc,
+                                               long long n_steps);
+/* One training sample from the sums instance i of h has accumulated since its last
+ * reset (read in place on the device), then resets them: calls after every window of
+ * steps give consecutive samples.  Synchronises. */
+DSMC_API dsmc_status dsmc_surrogate_add_run(dsmc_surrogate_handle s, dsmc_handle h, int i);
+/* Fit and select all models on the samples so far.  Synchronises. */
+DSMC_API dsmc_status dsmc_surrogate_train(dsmc_surrogate_handle s, dsmc_surrogate_fit* out);
+/* Monte Carlo bands (Sec. 2.3): n_trials trials, each drawing the selected models'
+ * weights as m + L z (S = L L^T) with z the trial's row of 4 standard normals
+ * (slip coefficient, a_1..a_3; host or device), solving Eq. 8 on n_cfd cells
+ * (cell-centred finite volume, wall values through ghost cells); u_mean and u_std
+ * (NULL to skip; sample standard deviation) get n_cfd values.  fit = NULL uses the
+ * last dsmc_surrogate_train.  Synchronises. */
+DSMC_API dsmc_status dsmc_surrogate_profile(dsmc_surrogate_handle s,
+                                            const dsmc_surrogate_fit* fit, int n_cfd,
+                                            const double* z, int n_trials, double* u_mean,
+                                            double* u_std);
+
 /* Tuner of the step partition.  For span sizes 1024, 2048, ... particles (those whose
  * shared memory fits, skipping sizes that give the same partition) it runs one
  * untimed and steps_per_trial timed steps, keeps the fastest, and stores it in the

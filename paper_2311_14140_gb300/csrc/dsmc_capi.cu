@@ -1096,6 +1096,16 @@ dsmc_status dsmc_channel_sums(dsmc_handle h, double* out) {
   return DSMC_OK;
 }
 
+dsmc_status dsmc_device_moments_of(dsmc_handle h, int id, const double** acc) {
+  dsmc_status s = check_index(h, id);
+  if (s != DSMC_OK) return s;
+  if (!acc) return fail(DSMC_E_INVAL, "acc: NULL");
+  DeviceGuard guard(h->device);
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
+  *acc = h->acc + (size_t)h->inst[id].cell_base * kNMom;
+  return DSMC_OK;
+}
+
 int dsmc_batch_size(dsmc_handle h) { return h ? h->n_inst() : 0; }
 
 int dsmc_id_bound(dsmc_handle h) { return h ? (int)h->inst.size() : 0; }

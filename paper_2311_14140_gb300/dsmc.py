@@ -86,6 +86,17 @@ class RequestResult(ctypes.Structure):
                 ("sum_vx", ctypes.c_double), ("converged", ctypes.c_int), ("id", ctypes.c_int)]
 
 
+class SurrogateFit(ctypes.Structure):
+    D = ctypes.c_double
+    _fields_ = [("n_samples", ctypes.c_longlong), ("n_v", D), ("n_c", D),
+                ("log_evidence_v", D * 2), ("prob_v", D * 2), ("alpha_v", D * 2),
+                ("beta_v", D * 2), ("sigma_p", D), ("sigma_p_var", D),
+                ("iterations_v", ctypes.c_int), ("log_evidence_c", D * 4), ("prob_c", D * 4),
+                ("alpha_c", D * 4), ("beta_c", D * 4), ("m_c", (D * 3) * 4),
+                ("S_c", (D * 9) * 4), ("iterations_c", ctypes.c_int * 4),
+                ("sel_v", ctypes.c_int), ("sel_c", ctypes.c_int), ("b", D * 3)]
+
+
 _lib = None
 
 
@@ -145,6 +156,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                             c.POINTER(RequestResult)]),
         "dsmc_solve": (st, [c.POINTER(Request), c.POINTER(Options), c.POINTER(ServeOptions),
                             c.POINTER(RequestResult)]),
+        "dsmc_device_moments_of": (st, [H, c.c_int, c.POINTER(c.c_void_p)]),
+        "dsmc_surrogate_exponents": (st, [c.c_double, c.c_void_p]),
+        "dsmc_surrogate_create": (st, [c.c_double, c.c_double, c.c_int, c.c_int, c.c_void_p,
+                                       c.c_void_p, c.POINTER(H)]),
+        "dsmc_surrogate_destroy": (st, [H]),
+        "dsmc_surrogate_reset": (st, [H]),
+        "dsmc_surrogate_add_window": (st, [H, c.c_void_p, c.c_longlong]),
+        "dsmc_surrogate_add_run": (st, [H, H, c.c_int]),
+        "dsmc_surrogate_train": (st, [H, c.POINTER(SurrogateFit)]),
+        "dsmc_surrogate_profile": (st, [H, c.POINTER(SurrogateFit), c.c_int, c.c_void_p, c.c_int,
+                                        c.c_void_p, c.c_void_p]),
         "dsmc_kernel_count": (c.c_int, []),
         "dsmc_kernel_name": (c.c_char_p, [c.c_int]),
         "dsmc_kernel_times": (st, [H, c.c_void_p, c.c_void_p]),
@@ -288,6 +310,12 @@ class Dsmc:
 
     def state_into(self, y=None, vx=None, vy=None, vz=None) -> None:
         _check(self._lib.dsmc_copy_state(self._h, _ptr(y), _ptr(vx), _ptr(vy), _ptr(vz)))
+
+    def device_moments(self) -> int:
+        """Device address of the moment sums (n_cells x 13 binary64)."""
+        p = ctypes.c_void_p()
+        _check(self._lib.dsmc_device_moments_of(self._h, 0, ctypes.byref(p)))
+        return p.value
 
     def cells(self):
         off = np.empty(self.n_cells + 1, np.int32)
@@ -572,6 +600,84 @@ def solve(request: dict, *, epoch_steps: int = 32, batches: int = 16, **opts) ->
     _check(load_library().dsmc_solve(ctypes.byref(r), ctypes.byref(o), ctypes.byref(so),
                                       ctypes.byref(res)))
     return {k: getattr(res, k) for k, _ in RequestResult._fields_}
+
+
+def _fit_dict(f: SurrogateFit) -> dict:
+    out = {}
+    for k, _ in SurrogateFit._fields_:
+        v = getattr(f, k)
+        if isinstance(v, ctypes.Array):
+            v = np.ctypeslib.as_array(v).copy()
+        out[k] = v
+    out["_raw"] = SurrogateFit.from_buffer_copy(f)
+    return out
+
+
+class Surrogate:
+    """The surrogate stage (``dsmc_surrogate_*``): training samples from windows of
+    moment sums, model fitting and selection, Monte Carlo bands of the corrected
+    macroscopic profile."""
+
+    def __init__(self, Kn: float, F: float, n_cells: int, ppc: int, b=None, stream=None):
+        L = load_library()
+        self._lib = L
+        self.n_cells = int(n_cells)
+        bb = None if b is None else np.ascontiguousarray(b, np.float64)
+        h = ctypes.c_void_p()
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = None
+        _check(L.dsmc_surrogate_create(float(Kn), float(F), self.n_cells, int(ppc), _ptr(bb),
+                                       int(stream) if stream else None, ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.dsmc_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self) -> None:
+        _check(self._lib.dsmc_surrogate_reset(self._h))
+
+    def add_window(self, acc, n_steps: int) -> None:
+        a = np.ascontiguousarray(acc, np.float64) if isinstance(acc, np.ndarray) else acc
+        _check(self._lib.dsmc_surrogate_add_window(self._h, _ptr(a), int(n_steps)))
+
+    def add_run(self, run, i: int = 0) -> None:
+        """One sample from what run (Dsmc, DsmcBatch or DsmcPool) instance i has sampled
+        since its last reset; resets it."""
+        _check(self._lib.dsmc_surrogate_add_run(self._h, run._h, int(i)))
+
+    def train(self) -> dict:
+        f = SurrogateFit()
+        _check(self._lib.dsmc_surrogate_train(self._h, ctypes.byref(f)))
+        return _fit_dict(f)
+
+    def profile(self, n_cfd: int, z, fit: Optional[dict] = None):
+        zz = np.ascontiguousarray(z, np.float64)
+        assert zz.ndim == 2 and zz.shape[1] == 4
+        mean = np.empty(int(n_cfd), np.float64)
+        sd = np.empty(int(n_cfd), np.float64)
+        fp = ctypes.byref(fit["_raw"]) if fit is not None else None
+        _check(self._lib.dsmc_surrogate_profile(self._h, fp, int(n_cfd), _ptr(zz), zz.shape[0],
+                                                _ptr(mean), _ptr(sd)))
+        return mean, sd
+
+
+def surrogate_exponents(Kn: float):
+    b = np.empty(3, np.float64)
+    _check(load_library().dsmc_surrogate_exponents(float(Kn), _ptr(b)))
+    return tuple(float(x) for x in b)
 
 
 def fields(acc, n_samples: int, ppc: int) -> dict:

@@ -101,3 +101,28 @@ def serving_requests(n: int = 2000, rate: float = 50.0, target_se: float = 0.01,
                         body_force=w.body_force, seed=w.seeds[0], arrival=float(t[i]),
                         target_se=float(target_se), max_steps=int(max_steps)))
     return out
+
+
+def synthetic_windows(n_windows: int, n_cells: int, per_cell: int, u, cxy, seed: int = 0):
+    """Raw moment sums of `n_windows` windows of synthetic samples: in every window and
+    cell i, `per_cell` velocity triples with vx ~ N(u[i], 1/2), vy ~ N(0, 1/2) with
+    covariance cxy[i] with vx, vz ~ N(0, 1/2), summed into the 13 raw moments
+    [count, vx, vy, vz, vx^2, vy^2, vz^2, vx vy, vx vz, vy vz, vx v^2, vy v^2, vz v^2].
+    Returns an array [n_windows, n_cells, 13] (binary64)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    u = np.asarray(u, np.float64)
+    rho = np.asarray(cxy, np.float64) / 0.5
+    s = math.sqrt(0.5)
+    out = np.empty((n_windows, n_cells, 13))
+    for w in range(n_windows):
+        z = rng.standard_normal((3, n_cells, per_cell))
+        vx = u[:, None] + s * z[0]
+        vy = s * (rho[:, None] * z[0] + np.sqrt(1.0 - rho[:, None] ** 2) * z[1])
+        vz = s * z[2]
+        v2 = vx * vx + vy * vy + vz * vz
+        cols = [np.ones_like(vx), vx, vy, vz, vx * vx, vy * vy, vz * vz, vx * vy, vx * vz,
+                vy * vz, vx * v2, vy * v2, vz * v2]
+        for k, c in enumerate(cols):
+            out[w, :, k] = c.sum(axis=1)
+    return out

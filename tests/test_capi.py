@@ -5,6 +5,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2311_14140_gb300 import dsmc as D
@@ -137,7 +138,7 @@ def test_binding_structs_match_the_header(tmp_path):
     structs = {"dsmc_gas": D.Gas, "dsmc_options": D.Options, "dsmc_info": D.Info,
                "dsmc_instance": D.Instance, "dsmc_pool_limits": D.PoolLimits,
                "dsmc_request": D.Request, "dsmc_serve_options": D.ServeOptions,
-               "dsmc_request_result": D.RequestResult}
+               "dsmc_request_result": D.RequestResult, "dsmc_surrogate_fit": D.SurrogateFit}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dsmc.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -187,6 +188,18 @@ def test_serve_arguments_are_checked(lib):
     bad = D.serve_options(batches=1)
     r2 = (D.Request * 1)(D.Request(inst, 0.0, 0.01, 100))
     assert lib.dsmc_solve(r2, None, ctypes.byref(bad), res) == 1
+
+
+def test_surrogate_table_and_arguments(lib):
+    """The library's own copy of Table 1 (typed from the paper) equals the printed one."""
+    rows = np.loadtxt(os.path.join(ROOT, "tests", "golden", "table1_exponents.txt"))
+    for kn, b1, b2, b3 in rows:
+        assert D.surrogate_exponents(kn) == (b1, b2, b3)
+    h = ctypes.c_void_p()
+    for args in ((0.0, 1e-3, 10, 5), (1.0, 0.0, 10, 5), (1.0, 1e-3, 2, 5), (1.0, 1e-3, 10, 0)):
+        assert lib.dsmc_surrogate_create(*args, None, None, ctypes.byref(h)) == 1
+    assert lib.dsmc_surrogate_train(None, None) == 1
+    assert lib.dsmc_surrogate_destroy(None) == 0
 
 
 def test_null_handle_calls_fail_cleanly(lib):
