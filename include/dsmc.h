@@ -94,6 +94,9 @@ typedef struct dsmc_options {
                              creation, or what dsmc_autotune chose), else 1024..2^24.
                              Only the work split changes: results are identical for
                              every value; default 0 */
+  int cta_warps;          /* warps per CTA of the collide/move pass: 0 keeps the shape
+                             in use (8 at creation, or what dsmc_autotune chose), else 4
+                             or 8; results are identical; default 0 */
   int graph;              /* 1: dsmc_step replays the launches of 16 steps as one
                              CUDA graph (captured on first use; needs a stream other
                              than the legacy default; off while profiling); results
@@ -121,6 +124,7 @@ typedef struct dsmc_info {
   size_t device_bytes; /* device memory the whole handle uses */
   int n_instances;     /* instances in the handle */
   int span_particles;  /* particles per span of the partition in use */
+  int cta_warps;       /* warps per CTA of the collide/move pass in use */
   int cells_per_span;  /* this instance's cells per span of the step passes */
   int n_spans;         /* this instance's spans (CTAs of the collide/move pass) */
   int total_spans;     /* spans of all instances */
@@ -421,10 +425,10 @@ DSMC_API dsmc_status dsmc_surrogate_profile(dsmc_surrogate_handle s,
                                             const double* z, int n_trials, double* u_mean,
                                             double* u_std);
 
-/* Tuner of the step partition.  For span sizes 1024, 2048, ... particles (those whose
- * shared memory fits, skipping sizes that give the same partition) it runs one
- * untimed and steps_per_trial timed steps, keeps the fastest, and stores it in the
- * handle's options (span_particles).  The trial steps are real steps of the run: they
+/* Tuner of the step's work split.  For CTA shapes of 8 and 4 warps and span sizes
+ * 1024, 2048, ... particles (those whose shared memory fits, skipping sizes that give
+ * the same partition) it runs one untimed and steps_per_trial timed steps, keeps the
+ * fastest, and stores it in the handle's options (cta_warps, span_particles).  The trial steps are real steps of the run: they
  * advance every instance, and since the partition does not change results the run is
  * the same as without tuning.  *best_span_particles and *best_ms_per_step (either may
  * be NULL) get the choice and its time per step.  Synchronises. */

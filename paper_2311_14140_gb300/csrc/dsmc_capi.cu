@@ -134,6 +134,8 @@ dsmc_status check_options(const dsmc_options* o) {
   if (o->span_particles != 0 &&
       (o->span_particles < kMinSpanParticles || o->span_particles > kMaxSpanParticles))
     return fail(DSMC_E_INVAL, "options: span_particles must be 0 or 1024..2^24");
+  if (o->cta_warps != 0 && o->cta_warps != kAWarps && o->cta_warps != kAWarpsSmall)
+    return fail(DSMC_E_INVAL, "options: cta_warps must be 0, 4 or 8");
   if (o->graph && o->stream == nullptr)
     return fail(DSMC_E_INVAL, "options: graph replay needs a stream other than the legacy default");
   return DSMC_OK;
@@ -331,6 +333,7 @@ struct dsmc_sim {
   std::vector<int> order;  // active ids in table order
   long long gstep = 0;     // steps this handle has launched
   int span_target = kDefaultSpanParticles;
+  int cta_warps = kAWarps;  // warps per CTA of the collide/move pass
   int spans = 0, max_cps = 1, max_cells = 1;  // partition in use
   int spans_reserved = 0;
   Capacity C{};
@@ -415,9 +418,10 @@ dsmc_status collect_times(dsmc_sim* h) {
   return DSMC_OK;
 }
 
-// The step passes must fit one CTA's shared memory with this partition and group size.
-bool step_fits(int max_cells, int max_cps, int G) {
-  return step_smem_layout(max_cells, max_cps, G + G / 2 - 1).total <= kStepSmemMax;
+// The step passes must fit one CTA's shared memory with this partition, group size and
+// CTA shape.
+bool step_fits(int max_cells, int max_cps, int G, int warps = kAWarps) {
+  return step_smem_layout(max_cells, max_cps, G + G / 2 - 1, warps).total <= kStepSmemMax;
 }
 
 // The largest cells-per-span any active instance (and `extra`, if given) would use
@@ -530,6 +534,7 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   L.max_cells = h->max_cells;
   L.max_cps = h->max_cps;
   L.max_cap = h->cap();
+  L.warps = h->cta_warps;
   L.gstep = h->gstep;
   L.gstep_dev = h->capturing ? h->gstep_dev : nullptr;
   L.count_only = count_only ? 1 : 0;
@@ -630,6 +635,7 @@ dsmc_status admit_fresh(dsmc_sim* h) {
   SL.max_cells = mc;
   SL.max_cps = m;
   SL.max_cap = h->cap();
+  SL.warps = h->cta_warps;
   SL.gstep = h->gstep;
   SL.gstep_dev = nullptr;
   SL.count_only = 1;
@@ -779,7 +785,7 @@ dsmc_status add_instance(dsmc_sim* h, const dsmc_instance& d, int index, int n_d
                                   "time step undefined: set options.dt for infinite Kn");
   int mcps, mcells;
   partition_extent(h, h->span_target, &x, &mcps, &mcells);
-  if (!step_fits(mcells, mcps, h->opt.group_size))
+  if (!step_fits(mcells, mcps, h->opt.group_size, h->cta_warps))
     return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   // Find a free id and room in every array.
   int new_id = -1;
@@ -833,6 +839,7 @@ dsmc_status new_handle(const Capacity& C, const dsmc_options& opt, bool pool, vo
   h->C = C;
   h->L = layout_of(C);
   h->span_target = opt.span_particles ? opt.span_particles : kDefaultSpanParticles;
+  h->cta_warps = opt.cta_warps ? opt.cta_warps : kAWarps;
   h->ex_slots.reset(C.slots);
   h->ex_cells.reset(C.cells);
   h->ex_offs.reset(C.offs);
@@ -928,7 +935,7 @@ dsmc_status create_run(const dsmc_instance* defs, int n_inst, const dsmc_options
       mcps = std::max(mcps, cps);
       mcells = std::max(mcells, defs[i].n_cells);
     }
-    if (!step_fits(mcells, mcps, opt.group_size))
+    if (!step_fits(mcells, mcps, opt.group_size, opt.cta_warps ? opt.cta_warps : kAWarps))
       return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   }
   dsmc_sim* h = nullptr;
@@ -978,6 +985,7 @@ dsmc_status dsmc_default_options(dsmc_options* opt) {
   opt->collisions = 1;
   opt->profile = 0;
   opt->span_particles = 0;
+  opt->cta_warps = 0;
   opt->graph = 0;
   opt->stream = nullptr;
   return DSMC_OK;
@@ -1121,11 +1129,12 @@ dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt) {
     if (!derive_params(x.omega, x.Kn, x.F, x.ppc, *opt, &ps[id]))
       return fail(DSMC_E_INVAL, "time step undefined: set options.dt for infinite Kn");
   }
-  // span_particles = 0 keeps the partition in use (default or tuned).
+  // span_particles = 0 and cta_warps = 0 keep the partition and CTA shape in use.
   const int target_use = opt->span_particles ? opt->span_particles : h->span_target;
+  const int warps_use = opt->cta_warps ? opt->cta_warps : h->cta_warps;
   int mcps, mcells;
   partition_extent(h, target_use, nullptr, &mcps, &mcells);
-  if (!step_fits(mcells, mcps, opt->group_size))
+  if (!step_fits(mcells, mcps, opt->group_size, warps_use))
     return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   if (h->events_used) {
     s = collect_times(h);
@@ -1133,6 +1142,7 @@ dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt) {
   }
   h->opt = *opt;
   for (int id : h->order) h->inst[id].p = ps[id];
+  h->cta_warps = warps_use;
   if (target_use != h->span_target) set_partition(h, target_use);
   h->tab_dirty = true;
   drop_graph(h);  // launch shapes or the stream may have changed
@@ -1166,43 +1176,51 @@ dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_par
     cudaEventDestroy(e0);
     return fail(DSMC_E_CUDA, "event");
   }
-  int best = h->span_target;
+  int best = h->span_target, best_warps = h->cta_warps;
   double best_ms = -1.0;
-  long long last_sig = -1;
   dsmc_status r = DSMC_OK;
-  for (int target = kMinSpanParticles; target <= (1 << 17) && r == DSMC_OK; target *= 2) {
-    int mcps, mcells;
-    partition_extent(h, target, nullptr, &mcps, &mcells);
-    if (!step_fits(mcells, mcps, h->opt.group_size)) break;
-    // Skip targets that give the same partition as the last one.
-    long long sig = 0;
-    for (int id : h->order) {
-      int cps, ns;
-      make_spans(h->inst[id].n_cells, h->inst[id].ppc, target, &cps, &ns);
-      sig = (sig * 1000003 + cps) & 0x3fffffffffffLL;
+  const int shapes[2] = {kAWarps, kAWarpsSmall};
+  for (int w : shapes) {
+    long long last_sig = -1;
+    for (int target = kMinSpanParticles; target <= (1 << 17) && r == DSMC_OK; target *= 2) {
+      int mcps, mcells;
+      partition_extent(h, target, nullptr, &mcps, &mcells);
+      if (!step_fits(mcells, mcps, h->opt.group_size, w)) break;
+      // Skip targets that give the same partition as the last one.
+      long long sig = 0;
+      for (int id : h->order) {
+        int cps, ns;
+        make_spans(h->inst[id].n_cells, h->inst[id].ppc, target, &cps, &ns);
+        sig = (sig * 1000003 + cps) & 0x3fffffffffffLL;
+      }
+      if (sig == last_sig) continue;
+      last_sig = sig;
+      h->cta_warps = w;
+      set_partition(h, target);
+      // one untimed step with the new shape, then the timed trial
+      if ((r = step_n(h, 1)) != DSMC_OK) break;
+      if (cudaEventRecord(e0, st) != cudaSuccess) { r = fail(DSMC_E_CUDA, "event record"); break; }
+      if ((r = step_n(h, steps_per_trial)) != DSMC_OK) break;
+      if (cudaEventRecord(e1, st) != cudaSuccess) { r = fail(DSMC_E_CUDA, "event record"); break; }
+      if (cudaEventSynchronize(e1) != cudaSuccess) { r = fail(DSMC_E_CUDA, "event sync"); break; }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per = ms / steps_per_trial;
+      if (best_ms < 0.0 || per < best_ms) {
+        best_ms = per;
+        best = target;
+        best_warps = w;
+      }
     }
-    if (sig == last_sig) continue;
-    last_sig = sig;
-    set_partition(h, target);
-    // one untimed step with the new partition, then the timed trial
-    if ((r = step_n(h, 1)) != DSMC_OK) break;
-    if (cudaEventRecord(e0, st) != cudaSuccess) { r = fail(DSMC_E_CUDA, "event record"); break; }
-    if ((r = step_n(h, steps_per_trial)) != DSMC_OK) break;
-    if (cudaEventRecord(e1, st) != cudaSuccess) { r = fail(DSMC_E_CUDA, "event record"); break; }
-    if (cudaEventSynchronize(e1) != cudaSuccess) { r = fail(DSMC_E_CUDA, "event sync"); break; }
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    const double per = ms / steps_per_trial;
-    if (best_ms < 0.0 || per < best_ms) {
-      best_ms = per;
-      best = target;
-    }
+    if (r != DSMC_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (r != DSMC_OK) return r;
+  h->cta_warps = best_warps;
   set_partition(h, best);
   h->opt.span_particles = best;
+  h->opt.cta_warps = best_warps;
   if (best_span_particles) *best_span_particles = best;
   if (best_ms_per_step) *best_ms_per_step = best_ms;
   if (h->opt.profile) return collect_times(h);
@@ -1405,6 +1423,7 @@ dsmc_status dsmc_get_info_of(dsmc_handle h, int id, dsmc_info* info) {
   info->device_bytes = h->L.total;
   info->n_instances = h->n_inst();
   info->span_particles = h->span_target;
+  info->cta_warps = h->cta_warps;
   info->cells_per_span = x.cps;
   info->n_spans = x.n_spans;
   info->total_spans = h->spans;

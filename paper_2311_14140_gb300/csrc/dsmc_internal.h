@@ -10,7 +10,8 @@ namespace dsmc {
 
 constexpr int kNMom = 13;          // raw moment sums per cell
 constexpr int kMaxGroup = 512;     // largest collision group size G
-constexpr int kAWarps = 8;         // warps per CTA of the collide/move pass
+constexpr int kAWarps = 8;         // warps per CTA of the collide/move pass (default)
+constexpr int kAWarpsSmall = 4;    // the other CTA shape the tuner may choose
 constexpr int kBWarpsMax = 4;      // warps (spans) per CTA of the span scatter
 constexpr int kMaxStepCells = 16384;
 constexpr int kMaxSpans = 152 * 16;   // rows of the per-step sort matrix, at most
@@ -104,7 +105,8 @@ struct StepSmem {
 
 __host__ __device__ inline size_t step_align(size_t o, size_t a) { return (o + a - 1) / a * a; }
 
-__host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int cap) {
+__host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int cap,
+                                                     int warps = kAWarps) {
   StepSmem L;
   size_t o = 0;
   L.hist = o;
@@ -130,7 +132,7 @@ __host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int c
   w += 8;
   L.per_warp = step_align(w, 128);
   L.warps = o;
-  o += (size_t)kAWarps * L.per_warp;
+  o += (size_t)warps * L.per_warp;
   L.total = o;
   return L;
 }
@@ -162,6 +164,7 @@ struct StepLaunch {
   int max_cells;         // largest n_cells of the instances
   int max_cps;
   int max_cap;
+  int warps;             // warps per CTA of the collide/move pass (kAWarps or kAWarpsSmall)
   long long gstep;       // global step number
   long long* gstep_dev;  // non-NULL (graph replay): read the step number here instead;
                          // the cell-offset kernel advances it at the end of the step

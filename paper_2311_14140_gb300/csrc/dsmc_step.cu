@@ -189,8 +189,8 @@ __device__ __forceinline__ const InstParams& stage_instance(const InstParams& on
 
 // Collision models (a.mode): 0 hard spheres, 1 VHS with 0.5 < omega < 1, 2 omega = 1
 // (sigma g independent of g).
-template <bool kBatch>
-__global__ void __launch_bounds__(kAWarps * 32, 3)
+template <bool kBatch, int kWarps>
+__global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
     k_collide_move(float4* __restrict__ P, const int* __restrict__ off_all,
                    const float* __restrict__ smax_in_all, float* __restrict__ smax_out_all,
                    unsigned long long* __restrict__ ncand_all,
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kAWarps * 32, 3)
   const int cps = a.cps;
   const int cap = a.cap;
   const int G = a.G;
-  const StepSmem L = step_smem_layout(n_cells, cps, cap);
+  const StepSmem L = step_smem_layout(n_cells, cps, cap, kWarps);
   int* h = reinterpret_cast<int*>(smem + L.hist);
   double* cacc = reinterpret_cast<double*>(smem + L.cell_acc);
   unsigned long long* ccand = reinterpret_cast<unsigned long long*>(smem + L.cell_cand);
@@ -775,14 +775,26 @@ cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 unsigned long long* nacc, double* acc, int* hist,
                                 const InstParams& one, const StepLaunch& L, int* err,
                                 cudaStream_t st) {
-  const StepSmem S = step_smem_layout(L.max_cells, L.max_cps, L.max_cap);
-  const dim3 block(kAWarps * 32);
-  if (L.n_inst == 1)
-    k_collide_move<false><<<L.n_spans_total, block, S.total, st>>>(
-        P, off, smax_in, smax_out, ncand, nacc, acc, hist, one, L, err);
-  else
-    k_collide_move<true><<<L.n_spans_total, block, S.total, st>>>(
-        P, off, smax_in, smax_out, ncand, nacc, acc, hist, one, L, err);
+  const bool small = L.warps == kAWarpsSmall;
+  const int warps = small ? kAWarpsSmall : kAWarps;
+  const StepSmem S = step_smem_layout(L.max_cells, L.max_cps, L.max_cap, warps);
+  const dim3 block(warps * 32);
+#define DSMC_COLLIDE(B, W)                                                                   \
+  k_collide_move<B, W><<<L.n_spans_total, block, S.total, st>>>(P, off, smax_in, smax_out, \
+                                                                ncand, nacc, acc, hist, one, \
+                                                                L, err)
+  if (L.n_inst == 1) {
+    if (small)
+      DSMC_COLLIDE(false, kAWarpsSmall);
+    else
+      DSMC_COLLIDE(false, kAWarps);
+  } else {
+    if (small)
+      DSMC_COLLIDE(true, kAWarpsSmall);
+    else
+      DSMC_COLLIDE(true, kAWarps);
+  }
+#undef DSMC_COLLIDE
   return cudaGetLastError();
 }
 
@@ -859,15 +871,17 @@ cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const 
 }
 
 cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes) {
-  cudaError_t e;
-  e = cudaFuncSetAttribute(k_collide_move<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)a_bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_collide_move<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)a_bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_scatter_spans<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)b_bytes);
+  const void* collide[4] = {(const void*)k_collide_move<false, kAWarps>,
+                            (const void*)k_collide_move<true, kAWarps>,
+                            (const void*)k_collide_move<false, kAWarpsSmall>,
+                            (const void*)k_collide_move<true, kAWarpsSmall>};
+  for (const void* f : collide) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_scatter_spans<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_scatter_spans<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)b_bytes);

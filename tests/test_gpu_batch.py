@@ -127,15 +127,15 @@ def test_moments_all_is_the_concatenation():
         assert ns[i] == n == 6
 
 
-@pytest.mark.parametrize("span", [1024, 4096, 65536])
-def test_partition_does_not_change_results(span):
+@pytest.mark.parametrize("span,warps", [(1024, 8), (4096, 4), (65536, 8), (2048, 4)])
+def test_partition_does_not_change_results(span, warps):
     ref = batch(DEFS)
     ref.step(10)
-    b = batch(DEFS, span_particles=span)
+    b = batch(DEFS, span_particles=span, cta_warps=warps)
     b.step(4)
-    b.set_options(span_particles=2048)
+    b.set_options(span_particles=2048, cta_warps=12 - warps)
     b.step(3)
-    b.set_options(span_particles=span)
+    b.set_options(span_particles=span, cta_warps=warps)
     b.step(3)
     for i in range(len(DEFS)):
         assert_same_run(Member(ref, i), Member(b, i))
@@ -152,6 +152,7 @@ def test_autotune_keeps_the_run():
     for i in range(len(DEFS)):
         assert_same_run(Member(ref, i), Member(b, i))
     assert b.info(0)["span_particles"] == best
+    assert b.info(0)["cta_warps"] in (4, 8)
 
 
 def test_graph_replay_matches_direct_launches():
