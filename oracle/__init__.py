@@ -74,6 +74,12 @@ def lib() -> ctypes.CDLL:
             L.or_move_particle.argtypes = [fp, fp, fp, fp, c.c_float, c.c_float,
                                            c.c_uint64, c.c_uint32, c.c_uint32]
             L.or_move_particle.restype = c.c_int
+            L.or_move_particle_open.argtypes = [fp, fp, fp, fp, c.c_float, c.c_float,
+                                                c.c_uint64, c.c_uint32, c.c_uint32, c.c_float,
+                                                c.c_float]
+            L.or_move_particle_open.restype = c.c_int
+            L.or_set_open_top.argtypes = [c.c_void_p, c.c_double, c.c_double]
+            L.or_set_open_top.restype = None
             L.or_scatter_pair.argtypes = [fp, fp, c.c_uint64, c.c_uint32, c.c_uint32,
                                           c.c_uint32, c.c_uint32]
             L.or_scatter_pair.restype = c.c_int
@@ -194,6 +200,16 @@ def move_particle(y, vx, vy, vz, dt, F, seed, step, slot):
     return tuple(v.value for v in a), bool(ok)
 
 
+def move_particle_open(y, vx, vy, vz, dt, F, seed, step, slot, u_top, p_top):
+    """One flight with the open Chapman-Enskog boundary at y = 1; returns the new
+    (y, vx, vy, vz) and the error bits."""
+    a = [ctypes.c_float(y), ctypes.c_float(vx), ctypes.c_float(vy), ctypes.c_float(vz)]
+    err = lib().or_move_particle_open(*[ctypes.byref(v) for v in a], float(dt), float(F),
+                                      int(seed), int(step) & 0xffffffff, int(slot),
+                                      float(u_top), float(p_top))
+    return tuple(v.value for v in a), int(err)
+
+
 def scatter_pair(vi, vj, seed, k, cell, step, group):
     a = (ctypes.c_float * 3)(*vi)
     b = (ctypes.c_float * 3)(*vj)
@@ -224,6 +240,11 @@ class OracleSim:
             self.close()
         except Exception:
             pass
+
+    def set_open_top(self, u: float, P: float) -> None:
+        """The boundary at y = 1 becomes an open Chapman-Enskog reservoir (bulk velocity
+        u, shear stress P) from the next step on."""
+        lib().or_set_open_top(self.h, float(u), float(P))
 
     def step(self, n=1) -> int:
         return lib().or_step(self.h, int(n))

@@ -107,6 +107,8 @@ OR_EXPORT void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
 #define OR_ERR_BOUNCES 2
 #define OR_ERR_SPHERE_ATTEMPTS 4
 #define OR_ERR_CANDIDATES 8
+#define OR_ERR_INFLOW_ATTEMPTS 64
+#define MAX_INFLOW_ATTEMPTS 30 /* sub-draws 16..45 */
 
 static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                  uint32_t out[4]) {
@@ -295,6 +297,9 @@ typedef struct {
   long long n_samples;
   long long step;
   int err;
+  /* open boundary at y = 1 (Chapman-Enskog reservoir), off by default */
+  int open_top;
+  float u_top, p_top;
 } osim;
 
 #define NMOM 13
@@ -360,16 +365,54 @@ static void init_particles(osim* s) {
   }
 }
 
+/* Re-emission into the gas below an open boundary at y = 1 that faces a gas in the
+ * first-order Chapman-Enskog state of a shear flow (the MMS hybrid's DSMC-CFD interface,
+ * Sec. 2 and Sec. 3.2: the CFD's velocity u and shear stress P there).  In units of
+ * Eq. 6 the velocity distribution is the Maxwellian of the peculiar velocity c times
+ * Gamma(c) = 1 + 2 P c_x c_y (this normalisation makes 2 <c_x c_y> = P, the stress
+ * estimator of the sampling), and particles enter with the flux weight |c_y|, c_y < 0.
+ * Attempt a (sub-draw 16 + a of the bounce's counter) proposes c_y = -sqrt(-ln u(w0)),
+ * (c_x, c_z) from one polar attempt on (w1, w2), and accepts when
+ * u(w3) (1 + 16 |P|) < Gamma(c) (rejection against the bound of Gamma for
+ * |c_x c_y| <= 8).  Returns 0 when the attempts ran out (then the last proposal, or the
+ * Maxwellian flux without shear, is used). */
+static int inflow_emission(uint64_t seed, uint32_t slot, uint32_t step, int b, float u_top,
+                           float p_top, float* vx, float* vy, float* vz) {
+  const float gmax = 1.0f + 16.0f * fabsf(p_top);
+  float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+  for (int a = 0; a < MAX_INFLOW_ATTEMPTS; ++a) {
+    uint32_t w[4];
+    draw(seed, slot, ((uint32_t)b << 8) | (16u + (uint32_t)a), step, TAG_MOVE << 24, w);
+    cy = -sqrtf(-or_ln(or_u01(w[0])));
+    float z0, z1;
+    if (!or_normal_pair(w[1], w[2], &z0, &z1)) continue;
+    cx = z0;
+    cz = z1;
+    float gam = 1.0f + 2.0f * p_top * cx * cy;
+    if (or_u01(w[3]) * gmax < gam) {
+      *vx = u_top + cx;
+      *vy = cy;
+      *vz = cz;
+      return 1;
+    }
+  }
+  *vx = u_top + cx;
+  *vy = cy;
+  *vz = cz;
+  return 0;
+}
+
 /* Free flight over one time step with the body force along x and fully diffuse
  * walls at the wall temperature (Sec. 2.1: plates at constant temperature, external
  * acceleration parallel to the plates).  A particle that crosses a wall is moved to
  * the wall after the fraction of the remaining time it needs, re-emitted with
  * |vy| = sqrt(-ln u) (flux-weighted half-Maxwellian) into the gas and vx, vz drawn
- * from N(0, 1/2), and flies on for the time left.  Returns 0 when the bounce limit
- * is hit. */
-OR_EXPORT int or_move_particle(float* py, float* pvx, float* pvy, float* pvz,
-                               float dt, float F, uint64_t seed, uint32_t step,
-                               uint32_t slot) {
+ * from N(0, 1/2), and flies on for the time left.  With open_top the boundary at y = 1
+ * is a Chapman-Enskog reservoir instead (inflow_emission).  Returns 0 when the
+ * bounce limit is hit; *err gets the error bits. */
+static int move_general(float* py, float* pvx, float* pvy, float* pvz, float dt, float F,
+                        uint64_t seed, uint32_t step, uint32_t slot, int open_top,
+                        float u_top, float p_top, int* err) {
   float y = *py, vx = *pvx, vy = *pvy, vz = *pvz;
   float t = dt;
   int ok = 1;
@@ -391,16 +434,26 @@ OR_EXPORT int or_move_particle(float* py, float* pvx, float* pvy, float* pvz,
     if (b >= MAX_BOUNCES) { /* leave the particle on the wall */
       y = wall;
       ok = 0;
+      *err |= OR_ERR_BOUNCES;
       break;
     }
     if (thit > t) thit = t;
     t = t - thit;
+    if (open_top && wall == 1.0f) {
+      if (!inflow_emission(seed, slot, step, b, u_top, p_top, &vx, &vy, &vz))
+        *err |= OR_ERR_INFLOW_ATTEMPTS;
+      y = wall;
+      continue;
+    }
     family f = {seed, slot, (uint32_t)b << 8, step, TAG_MOVE << 24, 1};
     uint32_t w[4];
     family_draw(&f, 0u, w);
     float speed = sqrtf(-or_ln(or_u01(w[0])));
     float z[2];
-    if (!family_normals(&f, z, 2)) ok = 0;
+    if (!family_normals(&f, z, 2)) {
+      ok = 0;
+      *err |= OR_ERR_NORMAL_ATTEMPTS;
+    }
     vx = z[0];
     vz = z[1];
     vy = (wall == 0.0f) ? speed : -speed;
@@ -408,6 +461,23 @@ OR_EXPORT int or_move_particle(float* py, float* pvx, float* pvy, float* pvz,
   }
   *py = y; *pvx = vx; *pvy = vy; *pvz = vz;
   return ok;
+}
+
+OR_EXPORT int or_move_particle(float* py, float* pvx, float* pvy, float* pvz,
+                               float dt, float F, uint64_t seed, uint32_t step,
+                               uint32_t slot) {
+  int err = 0;
+  int ok = move_general(py, pvx, pvy, pvz, dt, F, seed, step, slot, 0, 0.0f, 0.0f, &err);
+  return ok && !(err & OR_ERR_NORMAL_ATTEMPTS);
+}
+
+/* The same flight with the open boundary at y = 1; returns the error bits (0: none). */
+OR_EXPORT int or_move_particle_open(float* py, float* pvx, float* pvy, float* pvz, float dt,
+                                    float F, uint64_t seed, uint32_t step, uint32_t slot,
+                                    float u_top, float p_top) {
+  int err = 0;
+  move_general(py, pvx, pvy, pvz, dt, F, seed, step, slot, 1, u_top, p_top, &err);
+  return err;
 }
 
 /* sigma(g) g in units of sigma_ref v0: g for hard spheres, cvhs g^(2-2w) for VHS. */
@@ -596,15 +666,21 @@ static void sample_all(osim* s, double w) {
 }
 
 static void move_all(osim* s) {
-  for (int p = 0; p < s->N; ++p) {
-    if (!or_move_particle(&s->y[p], &s->vx[p], &s->vy[p], &s->vz[p], s->dt, s->F,
-                          s->seed, (uint32_t)s->step, (uint32_t)p))
-      s->err |= OR_ERR_BOUNCES;
-  }
+  for (int p = 0; p < s->N; ++p)
+    move_general(&s->y[p], &s->vx[p], &s->vy[p], &s->vz[p], s->dt, s->F, s->seed,
+                 (uint32_t)s->step, (uint32_t)p, s->open_top, s->u_top, s->p_top, &s->err);
 }
 
 /* ------------------------------------------------------------------------- */
 /* Public API (ctypes). */
+
+/* Makes the boundary at y = 1 an open Chapman-Enskog reservoir with bulk velocity u
+ * and shear stress P (rounded once to binary32), from the next step on. */
+OR_EXPORT void or_set_open_top(osim* s, double u, double P) {
+  s->open_top = 1;
+  s->u_top = (float)u;
+  s->p_top = (float)P;
+}
 
 OR_EXPORT void or_destroy(osim* s) {
   if (!s) return;

@@ -28,7 +28,8 @@ Readings where the paper is silent (each listed in the design notes):
 * a training sample is one window of sampled steps: per cell u = sum vx / N and
   P_xy = 2 n (<vx vy> - <vx><vy>) with n = N / (steps ppc) (Eq. 6 units);
 * du/dy at cell i is the central difference of the cell velocities; training points are
-  the cells that have both neighbours (N_P = n_cells - 2);
+  the cells that have both neighbours (N_P = n_cells - 2), or in a sub-domain of the MMS
+  hybrid the cells of the training region that have both neighbours;
 * the DSMC velocity at a wall is the linear extrapolation from the two nearest cell
   centres, u(wall) = 1.5 u_0 - 0.5 u_1;
 * P^CFD at the walls is the exact shear stress of the 1D problem, P(y) = F (2y - 1)
@@ -85,23 +86,33 @@ def basis(y, Kn: float, b):
     return np.stack(cols, axis=1)
 
 
-def training_sample(acc, n_steps: int, ppc: int, Kn: float, F: float, b):
+def training_sample(acc, n_steps: int, ppc: int, Kn: float, F: float, b, length: float = 1.0,
+                    n_train=None):
     """One training sample (Appendix A): the slip-model data and targets
-    (x = [-P(0), P(1)] = [F, F], t = DSMC wall velocities) and the constitutive-model
-    design rows and targets E_i = P_i + (2 Kn / sqrt(pi)) du/dy_i (Eq. 13) at the
-    interior cells."""
+    (x = -P(0) = F at the bottom wall and P(1) = F at the top, t = DSMC wall velocities)
+    and the constitutive-model design rows and targets E_i = P_i + (2 Kn / sqrt(pi))
+    du/dy_i (Eq. 13).
+
+    The run covers y in [0, length] (channel units) with its cells of equal width.
+    length = 1: the whole channel, both walls, training cells 1..n-2.  length < 1: a
+    DSMC sub-domain of the MMS hybrid above the bottom wall (Sec. 2, Sec. 3.2), the
+    bottom wall only, training cells 1..n_train-1 (the cells within the training
+    region; the rest is the buffer next to the interface)."""
     u, P = cell_fields(acc, n_steps, ppc)
     n = u.size
-    h = 1.0 / n
+    h = length / n
     y = (np.arange(n) + 0.5) * h
-    i = np.arange(1, n - 1)
+    last = n - 2 if length == 1.0 else int(n_train) - 1
+    i = np.arange(1, last + 1)
     dudy = (u[i + 1] - u[i - 1]) / (2.0 * h)
     E = P[i] + (2.0 * Kn / SQRT_PI) * dudy
     u_bot = 1.5 * u[0] - 0.5 * u[1]
-    u_top = 1.5 * u[n - 1] - 0.5 * u[n - 2]
-    p_bot, p_top = F * (2.0 * 0.0 - 1.0), F * (2.0 * 1.0 - 1.0)
-    return {"x_v": np.array([-p_bot, p_top]), "t_v": np.array([u_bot, u_top]),
-            "phi_c": basis(y[i], Kn, b), "t_c": E}
+    if length == 1.0:
+        u_top = 1.5 * u[n - 1] - 0.5 * u[n - 2]
+        x_v, t_v = np.array([F, F]), np.array([u_bot, u_top])
+    else:
+        x_v, t_v = np.array([F]), np.array([u_bot])
+    return {"x_v": x_v, "t_v": t_v, "phi_c": basis(y[i], Kn, b), "t_c": E}
 
 
 def log_evidence_zero(t):
