@@ -354,6 +354,16 @@ DSMC_API dsmc_status dsmc_serve(dsmc_handle pool, const dsmc_request* requests, 
 DSMC_API dsmc_status dsmc_solve(const dsmc_request* request, const dsmc_options* opt,
                                 const dsmc_serve_options* so, dsmc_request_result* result);
 
+/* Open boundary (the MMS hybrid's DSMC-CFD interface, Sec. 2 and Sec. 3.2): from the
+ * next step on, the boundary of instance i at y = 1 is a reservoir of gas in the
+ * first-order Chapman-Enskog state of a shear flow with bulk velocity u (along x) and
+ * shear stress P (Eq. 6 units, |P| <= 0.25), instead of a wall.  Each particle that
+ * crosses it is re-emitted into the run from the flux-weighted half-range distribution
+ * exp(-c^2) (1 + 2 P c_x c_y) |c_y|, c_y < 0 (c the peculiar velocity), so the number
+ * of particles is conserved; the boundary at y = 0 stays a diffuse wall.  u and P are
+ * rounded once to binary32; call again to update them (e.g. every hybrid iteration). */
+DSMC_API dsmc_status dsmc_set_open_top(dsmc_handle h, int i, double u, double P);
+
 /* The device address of instance i's moment sums (n_cells x DSMC_NMOM binary64, the
  * layout of dsmc_sample_moments), valid until the handle is destroyed or the instance
  * removed; its contents change with every step.  For consumers on the device. */
@@ -401,6 +411,15 @@ DSMC_API dsmc_status dsmc_surrogate_exponents(double Kn, double* b);
 DSMC_API dsmc_status dsmc_surrogate_create(double Kn, double F, int n_cells, int ppc,
                                            const double* b, void* stream,
                                            dsmc_surrogate_handle* out);
+/* A surrogate trained from runs that cover only the Knudsen layer next to the bottom
+ * wall (the MMS hybrid's DSMC sub-domain): the runs span y in [0, length] of the
+ * channel (0 < length < 1) with n_cells cells; the constitutive targets come from the
+ * cells 1 .. n_train - 1 of the training region (the rest is the buffer next to the
+ * interface) and the slip model from the bottom wall alone (x = -P(0) = F). */
+DSMC_API dsmc_status dsmc_surrogate_create_region(double Kn, double F, int n_cells, int ppc,
+                                                  double length, int n_train,
+                                                  const double* b, void* stream,
+                                                  dsmc_surrogate_handle* out);
 DSMC_API dsmc_status dsmc_surrogate_destroy(dsmc_surrogate_handle s);
 /* Forget all training samples. */
 DSMC_API dsmc_status dsmc_surrogate_reset(dsmc_surrogate_handle s);
@@ -424,6 +443,56 @@ DSMC_API dsmc_status dsmc_surrogate_profile(dsmc_surrogate_handle s,
                                             const dsmc_surrogate_fit* fit, int n_cfd,
                                             const double* z, int n_trials, double* u_mean,
                                             double* u_std);
+
+/* The MMS hybrid (Sec. 2, Sec. 3.2): DSMC only in the Knudsen layer next to the bottom
+ * wall (two mean free paths, Kn in channel units, rounded up to whole cells of width dy,
+ * plus `buffer` cells next to the interface; by symmetry it stands for both walls),
+ * open to the CFD through the Chapman-Enskog interface of dsmc_set_open_top, its
+ * windows training the surrogates (dsmc_surrogate_create_region) that correct the
+ * CFD, iterated.  Iteration k: interface velocity = the CFD's at y = L_d (mean of the
+ * two cells next to that face), stress F (2 L_d - 1); `steps` sampled steps (after
+ * `warmup` unsampled ones in the first iteration), one training sample per `window`
+ * steps, samples accumulating over iterations; retrain; CFD with the selected models.
+ * The first CFD profile is no-slip Navier-Stokes. */
+#define DSMC_MMS_MAX_ITER 64
+
+typedef struct dsmc_mms_params {
+  dsmc_gas gas;
+  double Kn;         /* channel Knudsen number */
+  double body_force; /* F of the channel (Eq. 6 units), != 0 */
+  double wall_T;
+  double dy;         /* DSMC cell width in channel units (Sec. 3: 0.005) */
+  int ppc;           /* particles per cell (Sec. 3: 50) */
+  int buffer;        /* buffer cells next to the interface (Sec. 3.2: 5) */
+  int iterations;    /* 1..DSMC_MMS_MAX_ITER */
+  int steps;         /* sampled steps per iteration */
+  int window;        /* steps per training sample (Sec. 3: 100) */
+  int warmup;        /* unsampled steps before the first samples */
+  int n_cfd;         /* CFD cells over the channel */
+  uint64_t seed;
+  int group_size;    /* 0: 256 */
+} dsmc_mms_params;
+
+typedef struct dsmc_mms_result {
+  int n_train, n_sub;          /* cells of the training region and of the sub-domain */
+  double L_d;                  /* sub-domain height (channel units) */
+  double b[3];                 /* exponents used (Table 1) */
+  int iterations_done;
+  double u_interface[DSMC_MMS_MAX_ITER]; /* interface velocity and stress of each */
+  double p_interface[DSMC_MMS_MAX_ITER]; /* iteration (the binary32 values used) */
+  long long samples;           /* training samples */
+  dsmc_surrogate_fit fit;      /* the last fit */
+} dsmc_mms_result;
+
+DSMC_API dsmc_status dsmc_default_mms_params(dsmc_mms_params* p);
+
+/* Runs the hybrid on `stream`.  profile[n_cfd] gets the final CFD profile with the
+ * selected models' posterior means; with n_trials > 0, z (n_trials x 4 standard
+ * normals, as for dsmc_surrogate_profile) gives band_sd[n_cfd] (NULL to skip), the
+ * Monte Carlo standard deviation.  Synchronises. */
+DSMC_API dsmc_status dsmc_mms_run(const dsmc_mms_params* p, void* stream, double* profile,
+                                  const double* z, int n_trials, double* band_sd,
+                                  dsmc_mms_result* out);
 
 /* Tuner of the step's work split.  For CTA shapes of 8 and 4 warps and span sizes
  * 1024, 2048, ... particles (those whose shared memory fits, skipping sizes that give

@@ -206,6 +206,8 @@ struct Inst {
   long long hist_base = 0;
   int cps = 0, n_spans = 0, span_base = 0;  // partition in use
   long long step = 0, n_samples = 0;
+  int open_top = 0;  // y = 1 an open Chapman-Enskog interface
+  float u_top = 0.0f, p_top = 0.0f;
 };
 
 // Sizes of the device arrays of a handle.
@@ -496,6 +498,9 @@ InstParams instance_params(const dsmc_sim* h, int id, int span_base) {
   a.mode = collision_mode(x.omega);
   a.id = id;
   a.smax0 = x.p.smax0;
+  a.open_top = x.open_top;
+  a.u_top = x.u_top;
+  a.p_top = x.p_top;
   return a;
 }
 
@@ -682,6 +687,7 @@ dsmc_status read_error_word(dsmc_sim* h) {
     if (v & kErrCandidates) what += " candidate-count";
     if (v & kErrSort) what += " sort-destination";
     if (v & kErrCopyTimeout) what += " bulk-copy-timeout";
+    if (v & kErrInflow) what += " inflow-attempts";
     return fail(DSMC_E_DEVICE_LIMIT, "device limit reached:" + what);
   }
   return DSMC_OK;
@@ -1111,6 +1117,19 @@ dsmc_status dsmc_device_moments_of(dsmc_handle h, int id, const double** acc) {
   DeviceGuard guard(h->device);
   if ((s = admit_fresh(h)) != DSMC_OK) return s;
   *acc = h->acc + (size_t)h->inst[id].cell_base * kNMom;
+  return DSMC_OK;
+}
+
+dsmc_status dsmc_set_open_top(dsmc_handle h, int id, double u, double P) {
+  dsmc_status s = check_index(h, id);
+  if (s != DSMC_OK) return s;
+  if (!std::isfinite(u) || !std::isfinite(P) || std::fabs(P) > 0.25)
+    return fail(DSMC_E_INVAL, "open boundary: finite u and |P| <= 0.25");
+  Inst& x = h->inst[id];
+  x.open_top = 1;
+  x.u_top = (float)u;
+  x.p_top = (float)P;
+  h->tab_dirty = true;
   return DSMC_OK;
 }
 

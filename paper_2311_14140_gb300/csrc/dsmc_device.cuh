@@ -18,6 +18,7 @@ constexpr uint32_t kStreamMove = 2u;
 constexpr uint32_t kStreamColl = 3u;
 
 constexpr int kNormalAttempts = 30;  // sub-draws 1..15, two attempts per draw
+constexpr int kInflowAttempts = 30;  // open-boundary emission: sub-draws 16..45
 constexpr int kMaxBounces = 64;
 
 
@@ -228,12 +229,51 @@ __device__ __forceinline__ int group_count(int nc, int G) {
   return ng;
 }
 
-// Free flight of one particle over dt with the body force along x and fully
-// diffuse walls at the wall temperature.  Returns false at the bounce limit.
+// Re-emission below an open boundary at y = 1 facing a gas in the first-order
+// Chapman-Enskog state of a shear flow (the MMS hybrid's DSMC-CFD interface): velocity
+// distribution exp(-c^2) (1 + 2 P c_x c_y) of the peculiar velocity c in the units of
+// Eq. 6, flux weight |c_y|, c_y < 0.  Attempt a (sub-draw 16 + a of the bounce's
+// counter) proposes c_y = -sqrt(-ln u(w0)) and (c_x, c_z) from one polar attempt on
+// (w1, w2), accepted when u(w3) (1 + 16 |P|) < 1 + 2 P c_x c_y.  Returns false when the
+// attempts ran out (the last proposal is kept).
+template <class Gen>
+__device__ __forceinline__ bool inflow_emission(float& vx, float& vy, float& vz, int b,
+                                                uint32_t step, uint32_t slot, float u_top,
+                                                float p_top, Gen gen) {
+  const float gmax = fadd(1.0f, fmul(16.0f, fabsf(p_top)));
+  const uint32_t c3 = kStreamMove << 24;
+  float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+  for (int a = 0; a < kInflowAttempts; ++a) {
+    const U4 w = gen(slot, ((uint32_t)b << 8) | (16u + (uint32_t)a), step, c3);
+    cy = -fsqrt(-ln32(u01(w.x)));
+    float z0, z1;
+    if (!polar_pair(w.y, w.z, z0, z1)) continue;
+    cx = z0;
+    cz = z1;
+    const float gam = fadd(1.0f, fmul(fmul(fmul(2.0f, p_top), cx), cy));
+    if (fmul(u01(w.w), gmax) < gam) {
+      vx = fadd(u_top, cx);
+      vy = cy;
+      vz = cz;
+      return true;
+    }
+  }
+  vx = fadd(u_top, cx);
+  vy = cy;
+  vz = cz;
+  return false;
+}
+
+// Free flight of one particle over dt with the body force along x and fully diffuse
+// walls at the wall temperature; with open_top the boundary at y = 1 is the open
+// Chapman-Enskog interface above.  Returns false at the bounce limit; inflow_fail is
+// set when an inflow emission ran out of attempts.
 // `gen(c0, c1, c2, c3)` is the Philox4x32-10 generator of the run's key.
 template <class Gen>
 __device__ __forceinline__ bool fly_with(float& y, float& vx, float& vy, float& vz, float dt,
-                                         float F, uint32_t step, uint32_t slot, Gen gen) {
+                                         float F, uint32_t step, uint32_t slot, Gen gen,
+                                         int open_top, float u_top, float p_top,
+                                         bool& inflow_fail) {
   float t = dt;
   bool ok = true;
   for (int b = 0;; ++b) {
@@ -256,6 +296,11 @@ __device__ __forceinline__ bool fly_with(float& y, float& vx, float& vy, float& 
     }
     if (thit > t) thit = t;
     t = fsub(t, thit);
+    if (open_top && wall == 1.0f) {
+      if (!inflow_emission(vx, vy, vz, b, step, slot, u_top, p_top, gen)) inflow_fail = true;
+      y = wall;
+      continue;
+    }
     const uint32_t c1 = (uint32_t)b << 8;
     const uint32_t c3 = kStreamMove << 24;
     U4 w = gen(slot, c1, step, c3);
@@ -281,20 +326,22 @@ __device__ __forceinline__ bool fly_with(float& y, float& vx, float& vy, float& 
 __device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, float dt,
                                     float F, uint32_t k0, uint32_t k1, uint32_t step,
                                     uint32_t slot) {
-  return fly_with(y, vx, vy, vz, dt, F, step, slot,
-                  [=](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-                    return philox(a, b, c, d, k0, k1);
-                  });
+  bool unused = false;
+  return fly_with(
+      y, vx, vy, vz, dt, F, step, slot,
+      [=](uint32_t a, uint32_t b, uint32_t c, uint32_t d) { return philox(a, b, c, d, k0, k1); },
+      0, 0.0f, 0.0f, unused);
 }
 
-// The same with the key's round keys precomputed.
+// The same with the key's round keys precomputed and the run's upper boundary.
 __device__ __forceinline__ bool fly(float& y, float& vx, float& vy, float& vz, float dt,
                                     float F, const PhiloxKeys& rk, uint32_t step,
-                                    uint32_t slot) {
-  return fly_with(y, vx, vy, vz, dt, F, step, slot,
-                  [&](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-                    return philox_rk(a, b, c, d, rk);
-                  });
+                                    uint32_t slot, int open_top, float u_top, float p_top,
+                                    bool& inflow_fail) {
+  return fly_with(
+      y, vx, vy, vz, dt, F, step, slot,
+      [&](uint32_t a, uint32_t b, uint32_t c, uint32_t d) { return philox_rk(a, b, c, d, rk); },
+      open_top, u_top, p_top, inflow_fail);
 }
 
 }  // namespace dsmc

@@ -28,6 +28,7 @@ constexpr int kErrSphere = 4;   // post-collision direction attempts ran out
 constexpr int kErrCandidates = 8;  // a group's candidate count exceeded kMaxCandidates
 constexpr int kErrSort = 16;       // a scatter destination fell outside [0, N)
 constexpr int kErrCopyTimeout = 32;  // a bulk copy into shared memory did not complete
+constexpr int kErrInflow = 64;       // an open-boundary emission ran out of attempts
 
 // Largest NTC candidate count of one group in one step (about 80 on the largest
 // workload): anything above means corrupted (sigma g)_max and is skipped.
@@ -95,6 +96,8 @@ struct InstParams {
   int mode;     // 0 hard spheres, 1 VHS (0.5 < omega < 1), 2 omega = 1
   int id;       // the instance's id in its handle
   float smax0;  // initial (sigma g)_max / sigma_ref of every cell
+  int open_top;        // 1: y = 1 is an open Chapman-Enskog interface
+  float u_top, p_top;  // its bulk velocity and shear stress
 };
 
 // Dynamic shared memory of one collide/move CTA (byte offsets).

@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
   const int n_groups = gfirst[c1 - c0];
 
   bool bad_bounce = false, sphere_fail = false, cand_fail = false, timeout = false;
+  bool inflow_fail = false;
   uint32_t parity = 0;
   int cur = -1;  // local cell the warp is gathering results for
   float gmax = 0.0f;
@@ -473,7 +474,8 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
         const int p = gs + i;
         const float4 r = rec[i];
         float yy = r.x, xx = r.y, uy = r.z, zz = r.w;
-        if (!fly(yy, xx, uy, zz, a.dt, a.F, a.keys, step, (uint32_t)(p - a.part_base)))
+        if (!fly(yy, xx, uy, zz, a.dt, a.F, a.keys, step, (uint32_t)(p - a.part_base),
+                 a.open_top, a.u_top, a.p_top, inflow_fail))
           bad_bounce = true;
         P[p] = make_float4(yy, xx, uy, zz);
         atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
@@ -491,6 +493,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
   if (sphere_fail) atomicOr(err, kErrSphere);
   if (cand_fail && lane == 0) atomicOr(err, kErrCandidates);
   if (timeout && lane == 0) atomicOr(err, kErrCopyTimeout);
+  if (inflow_fail) atomicOr(err, kErrInflow);
   __syncthreads();
 
   for (int i = threadIdx.x; i < n_cells; i += blockDim.x) row[i] = h[i];

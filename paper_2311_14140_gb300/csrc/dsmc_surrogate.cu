@@ -65,6 +65,9 @@ struct WindowArgs {
   double n_norm;   // steps * ppc: sampled count per cell at the initial density
   double kn, F;
   double b[3];
+  double length;   // the run's extent in channel units (1: the whole channel)
+  int last;        // last training cell (first is 1)
+  int both;        // 1: both walls give boundary data (whole channel), 0: bottom only
 };
 
 __device__ __forceinline__ double cell_u(const double* acc, int i) {
@@ -75,11 +78,11 @@ __global__ void __launch_bounds__(kThreads) k_window(const double* __restrict__ 
                                                      WindowArgs a, double* __restrict__ stats) {
   __shared__ double red[16][kThreads];
   const int t = threadIdx.x;
-  const double h = 1.0 / a.n;
+  const double h = a.length / a.n;
   const double c = 2.0 * a.kn / kSqrtPi;
   double g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0, p0 = 0, p1 = 0, p2 = 0, tt = 0,
          st = 0, nn = 0;
-  for (int i = 1 + t; i < a.n - 1; i += kThreads) {
+  for (int i = 1 + t; i <= a.last; i += kThreads) {
     const double* r = acc + (size_t)i * dsmc::kNMom;
     const double N = r[0];
     const double ux = r[1] / N, uy = r[2] / N;
@@ -123,15 +126,23 @@ __global__ void __launch_bounds__(kThreads) k_window(const double* __restrict__ 
     stats[12] += red[9][0];
     stats[13] += red[11][0];
     stats[18] += red[10][0];
-    // boundary models: x = (-P(0), P(1)) = (F, F), t = wall velocities
+    // boundary models: x = -P(0) = F (and P(1) = F), t = wall velocities
     const int n = a.n;
     const double ub = 1.5 * cell_u(acc, 0) - 0.5 * cell_u(acc, 1);
-    const double ut = 1.5 * cell_u(acc, n - 1) - 0.5 * cell_u(acc, n - 2);
-    stats[14] += a.F * ub + a.F * ut;
-    stats[15] += a.F * a.F + a.F * a.F;
-    stats[16] += ub * ub + ut * ut;
-    stats[17] += 2.0;
-    stats[19] += ub + ut;
+    if (a.both) {
+      const double ut = 1.5 * cell_u(acc, n - 1) - 0.5 * cell_u(acc, n - 2);
+      stats[14] += a.F * ub + a.F * ut;
+      stats[15] += a.F * a.F + a.F * a.F;
+      stats[16] += ub * ub + ut * ut;
+      stats[17] += 2.0;
+      stats[19] += ub + ut;
+    } else {
+      stats[14] += a.F * ub;
+      stats[15] += a.F * a.F;
+      stats[16] += ub * ub;
+      stats[17] += 1.0;
+      stats[19] += ub;
+    }
   }
 }
 
@@ -379,6 +390,8 @@ void probabilities(const double* le, int n, double* p) {
 struct dsmc_surrogate {
   double Kn = 1.0, F = 0.0;
   int n_cells = 0, ppc = 0;
+  double length = 1.0;  // extent of the runs in channel units
+  int n_train = 0;      // cells of the training region (sub-domain runs)
   double b[3]{};
   cudaStream_t stream = nullptr;
   double* stats = nullptr;    // device, kStats
@@ -432,6 +445,18 @@ dsmc_status dsmc_surrogate_create(double Kn, double F, int n_cells, int ppc, con
   return DSMC_OK;
 }
 
+dsmc_status dsmc_surrogate_create_region(double Kn, double F, int n_cells, int ppc,
+                                         double length, int n_train, const double* b,
+                                         void* stream, dsmc_surrogate_handle* out) {
+  if (!(length > 0.0 && length < 1.0) || n_train < 2 || n_train > n_cells - 1)
+    return reject(DSMC_E_INVAL, "surrogate region: 0 < length < 1, 2 <= n_train <= n_cells - 1");
+  dsmc_status st = dsmc_surrogate_create(Kn, F, n_cells, ppc, b, stream, out);
+  if (st != DSMC_OK) return st;
+  (*out)->length = length;
+  (*out)->n_train = n_train;
+  return DSMC_OK;
+}
+
 dsmc_status dsmc_surrogate_destroy(dsmc_surrogate_handle s) {
   if (!s) return DSMC_OK;
   cudaStreamSynchronize(s->stream);
@@ -458,6 +483,9 @@ static dsmc_status add_device_window(dsmc_surrogate* s, const double* acc_dev, l
   a.kn = s->Kn;
   a.F = s->F;
   for (int l = 0; l < 3; ++l) a.b[l] = s->b[l];
+  a.length = s->length;
+  a.both = s->length == 1.0 ? 1 : 0;
+  a.last = a.both ? s->n_cells - 2 : s->n_train - 1;
   k_window<<<1, kThreads, 0, s->stream>>>(acc_dev, a, s->stats);
   SUR_CUDA(cudaGetLastError(), "window kernel");
   s->n_samples += 1;

@@ -97,6 +97,25 @@ class SurrogateFit(ctypes.Structure):
                 ("sel_v", ctypes.c_int), ("sel_c", ctypes.c_int), ("b", D * 3)]
 
 
+MMS_MAX_ITER = 64
+
+
+class MmsParams(ctypes.Structure):
+    _fields_ = [("gas", Gas), ("Kn", ctypes.c_double), ("body_force", ctypes.c_double),
+                ("wall_T", ctypes.c_double), ("dy", ctypes.c_double), ("ppc", ctypes.c_int),
+                ("buffer", ctypes.c_int), ("iterations", ctypes.c_int), ("steps", ctypes.c_int),
+                ("window", ctypes.c_int), ("warmup", ctypes.c_int), ("n_cfd", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("group_size", ctypes.c_int)]
+
+
+class MmsResult(ctypes.Structure):
+    _fields_ = [("n_train", ctypes.c_int), ("n_sub", ctypes.c_int), ("L_d", ctypes.c_double),
+                ("b", ctypes.c_double * 3), ("iterations_done", ctypes.c_int),
+                ("u_interface", ctypes.c_double * MMS_MAX_ITER),
+                ("p_interface", ctypes.c_double * MMS_MAX_ITER),
+                ("samples", ctypes.c_longlong), ("fit", SurrogateFit)]
+
+
 _lib = None
 
 
@@ -157,6 +176,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsmc_solve": (st, [c.POINTER(Request), c.POINTER(Options), c.POINTER(ServeOptions),
                             c.POINTER(RequestResult)]),
         "dsmc_device_moments_of": (st, [H, c.c_int, c.POINTER(c.c_void_p)]),
+        "dsmc_set_open_top": (st, [H, c.c_int, c.c_double, c.c_double]),
+        "dsmc_surrogate_create_region": (st, [c.c_double, c.c_double, c.c_int, c.c_int,
+                                              c.c_double, c.c_int, c.c_void_p, c.c_void_p,
+                                              c.POINTER(H)]),
+        "dsmc_default_mms_params": (st, [c.POINTER(MmsParams)]),
+        "dsmc_mms_run": (st, [c.POINTER(MmsParams), c.c_void_p, c.c_void_p, c.c_void_p, c.c_int,
+                              c.c_void_p, c.POINTER(MmsResult)]),
         "dsmc_surrogate_exponents": (st, [c.c_double, c.c_void_p]),
         "dsmc_surrogate_create": (st, [c.c_double, c.c_double, c.c_int, c.c_int, c.c_void_p,
                                        c.c_void_p, c.POINTER(H)]),
@@ -311,6 +337,10 @@ class Dsmc:
     def state_into(self, y=None, vx=None, vy=None, vz=None) -> None:
         _check(self._lib.dsmc_copy_state(self._h, _ptr(y), _ptr(vx), _ptr(vy), _ptr(vz)))
 
+    def set_open_top(self, u: float, P: float) -> None:
+        """Makes y = 1 an open Chapman-Enskog interface (velocity u, stress P)."""
+        _check(self._lib.dsmc_set_open_top(self._h, 0, float(u), float(P)))
+
     def device_moments(self) -> int:
         """Device address of the moment sums (n_cells x 13 binary64)."""
         p = ctypes.c_void_p()
@@ -443,6 +473,9 @@ class _Multi:
 
     def size(self) -> int:
         return self._lib.dsmc_batch_size(self._h)
+
+    def set_open_top(self, i: int, u: float, P: float) -> None:
+        _check(self._lib.dsmc_set_open_top(self._h, int(i), float(u), float(P)))
 
     def moments(self, i: int, out=None):
         if out is None:
@@ -628,7 +661,10 @@ class Surrogate:
     moment sums, model fitting and selection, Monte Carlo bands of the corrected
     macroscopic profile."""
 
-    def __init__(self, Kn: float, F: float, n_cells: int, ppc: int, b=None, stream=None):
+    def __init__(self, Kn: float, F: float, n_cells: int, ppc: int, b=None, stream=None,
+                 length: float = 1.0, n_train: int = 0):
+        """length < 1: runs covering the Knudsen layer [0, length] of the channel, training
+        cells 1 .. n_train - 1 (``dsmc_surrogate_create_region``)."""
         L = load_library()
         self._lib = L
         self.n_cells = int(n_cells)
@@ -641,8 +677,14 @@ class Surrogate:
                     stream = torch.cuda.current_stream().cuda_stream
             except Exception:
                 stream = None
-        _check(L.dsmc_surrogate_create(float(Kn), float(F), self.n_cells, int(ppc), _ptr(bb),
-                                       int(stream) if stream else None, ctypes.byref(h)))
+        sp = int(stream) if stream else None
+        if length == 1.0:
+            _check(L.dsmc_surrogate_create(float(Kn), float(F), self.n_cells, int(ppc), _ptr(bb),
+                                           sp, ctypes.byref(h)))
+        else:
+            _check(L.dsmc_surrogate_create_region(float(Kn), float(F), self.n_cells, int(ppc),
+                                                  float(length), int(n_train), _ptr(bb), sp,
+                                                  ctypes.byref(h)))
         self._h = h
 
     def close(self) -> None:
@@ -682,6 +724,40 @@ class Surrogate:
         _check(self._lib.dsmc_surrogate_profile(self._h, fp, int(n_cfd), _ptr(zz), zz.shape[0],
                                                 _ptr(mean), _ptr(sd)))
         return mean, sd
+
+
+def mms_hybrid(Kn: float, F: float, *, omega: float = 0.5, dy: float = 0.005, ppc: int = 50,
+               buffer: int = 5, iterations: int = 5, steps: int = 2000, window: int = 100,
+               warmup: int = 1000, n_cfd: int = 200, seed: int = 0, group_size: int = 256,
+               z=None, stream=None) -> dict:
+    """The MMS hybrid (``dsmc_mms_run``): returns the final CFD profile, its Monte Carlo
+    standard deviation (when z, n_trials x 4 standard normals, is given), the interface
+    history and the last fit."""
+    L = load_library()
+    p = MmsParams()
+    _check(L.dsmc_default_mms_params(ctypes.byref(p)))
+    p.gas.omega = float(omega)
+    p.Kn, p.body_force, p.dy, p.ppc, p.buffer = float(Kn), float(F), float(dy), int(ppc), int(buffer)
+    p.iterations, p.steps, p.window, p.warmup = int(iterations), int(steps), int(window), int(warmup)
+    p.n_cfd, p.seed, p.group_size = int(n_cfd), int(seed) & 0xFFFFFFFFFFFFFFFF, int(group_size)
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except Exception:
+            stream = None
+    prof = np.empty(int(n_cfd), np.float64)
+    zz = None if z is None else np.ascontiguousarray(z, np.float64)
+    sd = None if z is None else np.empty(int(n_cfd), np.float64)
+    r = MmsResult()
+    _check(L.dsmc_mms_run(ctypes.byref(p), int(stream) if stream else None, _ptr(prof),
+                          _ptr(zz), 0 if zz is None else zz.shape[0], _ptr(sd), ctypes.byref(r)))
+    k = r.iterations_done
+    return {"profile": prof, "band_sd": sd, "n_train": r.n_train, "n_sub": r.n_sub,
+            "L_d": r.L_d, "b": tuple(r.b), "samples": r.samples,
+            "interface": [(r.u_interface[i], r.p_interface[i]) for i in range(k)],
+            "fit": _fit_dict(r.fit)}
 
 
 def surrogate_exponents(Kn: float):

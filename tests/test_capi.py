@@ -138,7 +138,8 @@ def test_binding_structs_match_the_header(tmp_path):
     structs = {"dsmc_gas": D.Gas, "dsmc_options": D.Options, "dsmc_info": D.Info,
                "dsmc_instance": D.Instance, "dsmc_pool_limits": D.PoolLimits,
                "dsmc_request": D.Request, "dsmc_serve_options": D.ServeOptions,
-               "dsmc_request_result": D.RequestResult, "dsmc_surrogate_fit": D.SurrogateFit}
+               "dsmc_request_result": D.RequestResult, "dsmc_surrogate_fit": D.SurrogateFit,
+               "dsmc_mms_params": D.MmsParams, "dsmc_mms_result": D.MmsResult}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dsmc.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -200,6 +201,22 @@ def test_surrogate_table_and_arguments(lib):
         assert lib.dsmc_surrogate_create(*args, None, None, ctypes.byref(h)) == 1
     assert lib.dsmc_surrogate_train(None, None) == 1
     assert lib.dsmc_surrogate_destroy(None) == 0
+
+
+def test_mms_arguments_are_checked(lib):
+    p = D.MmsParams()
+    assert lib.dsmc_default_mms_params(ctypes.byref(p)) == 0
+    assert (p.dy, p.ppc, p.buffer, p.n_cfd) == (0.005, 50, 5, 200)
+    r = D.MmsResult()
+    prof = np.empty(200)
+    p.Kn, p.body_force = 0.1, 0.0          # no force
+    assert lib.dsmc_mms_run(ctypes.byref(p), None, prof.ctypes.data, None, 0, None,
+                            ctypes.byref(r)) == 1
+    p.body_force, p.Kn = 1e-3, 0.3          # 2 lambda + buffer above half the channel
+    assert lib.dsmc_mms_run(ctypes.byref(p), None, prof.ctypes.data, None, 0, None,
+                            ctypes.byref(r)) == 1
+    assert "half the channel" in lib.dsmc_last_error().decode()
+    assert lib.dsmc_set_open_top(None, 0, 0.0, 0.0) == 1
 
 
 def test_null_handle_calls_fail_cleanly(lib):

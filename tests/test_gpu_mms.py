@@ -1,0 +1,129 @@
+"""The MMS hybrid on the GPU (Sec. 2, Sec. 3.2): the open Chapman-Enskog interface of
+the DSMC (bit for bit against the oracle's), surrogates trained on Knudsen-layer
+sub-domains (against the oracle on seeded synthetic windows), the whole hybrid
+iteration (against the oracle's), and the hybrid's profile against a DSMC of the whole
+channel (the paper's validation, §3.2)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mms as OM
+from oracle import surrogate as S
+from paper_2311_14140_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MOM_TOL = 2e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_14140_gb300 import _build
+    _build.build()
+
+
+@pytest.mark.parametrize("omega,Kn,u,P,at", [
+    (0.5, 0.5, 0.01, 0.02, 0), (0.81, 0.2, -0.005, -0.05, 7), (0.5, 2.0, 0.0, 0.0, 0),
+    (0.74, 0.05, 0.03, 0.1, 3)])
+def test_open_boundary_bitexact(omega, Kn, u, P, at):
+    from paper_2311_14140_gb300 import Dsmc
+    kw = dict(n_cells=45, ppc=60, seed=13)
+    o = oracle.OracleSim(omega=omega, Kn=Kn, F=2e-3, sample_start=2, **kw)
+    g = Dsmc(Kn, kw["n_cells"], kw["ppc"], omega=omega, body_force=2e-3, seed=kw["seed"],
+             sample_start=2)
+    o.step(at)
+    g.step(at)
+    o.set_open_top(u, P)
+    g.set_open_top(u, P)
+    o.step(25)
+    g.step(25)
+    assert o.error == 0
+    for name, a, b in zip(("y", "vx", "vy", "vz"), o.state(), g.state()):
+        bad = np.flatnonzero(a.view(np.uint32) != b.view(np.uint32))
+        assert bad.size == 0, f"{name}: {bad.size} slots differ"
+    for a, b in zip(o.cells(), g.cells()):
+        np.testing.assert_array_equal(a.view(np.uint32) if a.dtype == np.float32 else a,
+                                      b.view(np.uint32) if b.dtype == np.float32 else b)
+    mo, no = o.moments()
+    mg, ng = g.moments()
+    assert no == ng
+    assert np.all(np.abs(mg - mo) <= MOM_TOL * o.abs_moments())
+
+
+def test_region_surrogate_matches_oracle():
+    from paper_2311_14140_gb300 import Surrogate
+    Kn, F = 0.1, 5e-3
+    n_train, n_sub, L_d = OM.layer_geometry(Kn, 0.005, 5)
+    b = S.exponents(Kn)
+    y = (np.arange(n_sub) + 0.5) * 0.005
+    u = S.exact_profile(Kn, F, y, 1.15, (0.25,), b[:1])
+    cxy = 0.5 * F * (2 * y - 1)
+    wins = W.synthetic_windows(80, n_sub, 300, u, cxy, seed=31)
+    g = Surrogate(Kn, F, n_sub, 300, length=L_d, n_train=n_train)
+    samples = []
+    for w in wins:
+        g.add_window(w, 1)
+        samples.append(S.training_sample(w, 1, 300, Kn, F, b, length=L_d, n_train=n_train))
+    fg, fo = g.train(), S.train(samples, Kn)
+    assert fg["n_v"] == 80 and fg["n_c"] == 80 * (n_train - 1)
+    assert fg["sel_v"] == fo["sel_v"] and fg["sel_c"] == fo["sel_c"]
+    for i in range(2):
+        assert fg["log_evidence_v"][i] == pytest.approx(fo["v"][i]["log_evidence"], rel=1e-8)
+    for i in range(4):
+        assert fg["log_evidence_c"][i] == pytest.approx(fo["c"][i]["log_evidence"], rel=1e-8)
+    fv = fo["v"][1]
+    assert abs(fg["sigma_p"] - fv["m"][0]) <= 1e-6 * math.sqrt(fv["S"][0, 0])
+
+
+def test_hybrid_matches_oracle():
+    """A short hybrid (3 iterations) run by the library and by the oracle from the same
+    seed: the same interface history (binary32 values, so the DSMC layers ran bit for bit
+    alike), the same number of samples and selections, evidences to 1e-8, and the same
+    final profile."""
+    from paper_2311_14140_gb300 import mms_hybrid
+    kw = dict(ppc=40, iterations=3, steps=200, window=20, warmup=100, seed=4)
+    Kn, F = 0.1, 0.02
+    g = mms_hybrid(Kn, F, **kw)
+    o = OM.mms_hybrid(Kn, F, **kw)
+    assert o["error"] == 0
+    assert (g["n_train"], g["n_sub"], g["samples"]) == (o["n_train"], o["n_sub"], o["samples"])
+    assert g["interface"] == o["interface"]
+    fg, fo = g["fit"], o["fit"]
+    assert fg["sel_v"] == fo["sel_v"] and fg["sel_c"] == fo["sel_c"]
+    for i in range(4):
+        assert fg["log_evidence_c"][i] == pytest.approx(fo["c"][i]["log_evidence"], rel=1e-8)
+    # posterior means agree to ~1e-6 of their standard deviations (sufficient statistics
+    # against data, as in the surrogate parity tests), hence the profile to 1e-6 of its
+    # scale
+    fv = fo["v"][1]
+    assert abs(fg["sigma_p"] - fv["m"][0]) <= 1e-5 * math.sqrt(fv["S"][0, 0])
+    scale = np.abs(o["profile"]).max()
+    np.testing.assert_allclose(g["profile"], o["profile"], rtol=0, atol=1e-6 * scale)
+
+
+def test_hybrid_reproduces_the_whole_channel_dsmc():
+    """Kn = 0.1, Ma ~ 0.05 (the regime of §3): the hybrid, with DSMC only in the 2-lambda
+    layer (45 of 200 cells, 8 iterations of 8,000 steps), against a DSMC of the whole
+    channel (40,000 sampled steps).  Compared on 20-cell bins of the channel: within 3 %
+    of the peak velocity (the hybrid's own Monte Carlo band is ~2 % at the centre, the
+    benchmark's noise ~0.5 %), with the slip model selected."""
+    from paper_2311_14140_gb300 import Dsmc, fields, mms_hybrid
+    Kn, F = 0.1, 0.012
+    z = np.random.default_rng(5).standard_normal((1000, 4))
+    h = mms_hybrid(Kn, F, ppc=200, iterations=8, steps=8000, window=100, warmup=3000, seed=21,
+                   z=z)
+    assert h["fit"]["sel_v"] == 1
+    g = Dsmc(Kn, 200, 200, body_force=F, seed=22, sample_start=3001)
+    g.step(43000)
+    m, n = g.moments()
+    u_ref = fields(m, n, 200)["ux"]
+    bins = lambda x: x.reshape(10, 20).mean(axis=1)
+    err = np.abs(bins(h["profile"]) - bins(u_ref)).max() / np.abs(u_ref).max()
+    assert err < 0.03, err
+    # the bands are narrow next to the walls, wider in the bulk (Sec. 3.1)
+    assert h["band_sd"][0] <= h["band_sd"][100] * (1 + 1e-9)
