@@ -126,3 +126,37 @@ def synthetic_windows(n_windows: int, n_cells: int, per_cell: int, u, cxy, seed:
         for k, c in enumerate(cols):
             out[w, :, k] = c.sum(axis=1)
     return out
+
+
+def latin_hypercube(n: int, dims: int = 2, seed: int = 0):
+    """n points of a Latin hypercube in [0, 1]^dims: each axis cut into n equal strata,
+    one point per stratum, uniform within it, strata paired by independent
+    permutations."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    u = np.empty((n, dims))
+    for d in range(dims):
+        u[:, d] = (rng.permutation(n) + rng.uniform(size=n)) / n
+    return u
+
+
+# Range of the Gaussian-process variant's design (an item of the benchmark, not of the
+# paper): Kn log-uniform over the paper's verification range 0.1-5 (Sec. 3.1) and a
+# force factor in [0.5, 2] times F_ma(Kn), the force whose slip-Stokes channel-mean
+# speed is 0.02 v0 (Ma ~ 0.02).
+GP_KN = (0.1, 5.0)
+GP_FORCE = (0.5, 2.0)
+
+
+def gp_force(Kn: float, factor: float) -> float:
+    return factor * 0.02 / (math.sqrt(math.pi) / (12.0 * Kn) + 1.0)
+
+
+def gp_design(n: int = 64, seed: int = 3):
+    """The design points (Kn, F) of the GP variant and their unit-square coordinates."""
+    import numpy as np
+    u = latin_hypercube(n, 2, seed)
+    Kn = np.exp(np.log(GP_KN[0]) + u[:, 0] * (np.log(GP_KN[1]) - np.log(GP_KN[0])))
+    f = GP_FORCE[0] + u[:, 1] * (GP_FORCE[1] - GP_FORCE[0])
+    F = np.array([gp_force(k, x) for k, x in zip(Kn, f)])
+    return Kn, F, u
