@@ -433,6 +433,11 @@ DSMC_API dsmc_status dsmc_surrogate_add_window(dsmc_surrogate_handle s, const do
 DSMC_API dsmc_status dsmc_surrogate_add_run(dsmc_surrogate_handle s, dsmc_handle h, int i);
 /* Fit and select all models on the samples so far.  Synchronises. */
 DSMC_API dsmc_status dsmc_surrogate_train(dsmc_surrogate_handle s, dsmc_surrogate_fit* out);
+/* The stress correction S(y) (Eq. 14) of a fit's selected constitutive model (posterior
+ * means, the fit's exponents) at the n + 1 faces y = f / n of an n-cell CFD grid
+ * (host or device output; zeros for C0).  Synchronises. */
+DSMC_API dsmc_status dsmc_surrogate_correction(const dsmc_surrogate_fit* fit, int n,
+                                               double* S_faces, void* stream);
 /* Monte Carlo bands (Sec. 2.3): n_trials trials, each drawing the selected models'
  * weights as m + L z (S = L L^T) with z the trial's row of 4 standard normals
  * (slip coefficient, a_1..a_3; host or device), solving Eq. 8 on n_cfd cells
@@ -493,6 +498,33 @@ DSMC_API dsmc_status dsmc_default_mms_params(dsmc_mms_params* p);
 DSMC_API dsmc_status dsmc_mms_run(const dsmc_mms_params* p, void* stream, double* profile,
                                   const double* z, int n_trials, double* band_sd,
                                   dsmc_mms_result* out);
+
+/* Gaussian-process variant of the surrogate stage (an item of the benchmark's
+ * configurations, not the paper's method): GP regression (Rasmussen and Williams 2006,
+ * Ch. 2) over n <= DSMC_GP_MAX_POINTS design points X (n x 2, row-major, inputs scaled
+ * to the unit square) with m output columns Y (n x m, row-major), squared-exponential
+ * covariance exp(-1/2 ((dx_1 / l_1)^2 + (dx_2 / l_2)^2)) plus noise s2 on the diagonal,
+ * each column standardised (mean, population standard deviation) and sharing the
+ * covariance.  dsmc_gp_fit evaluates the summed log marginal likelihood at each of
+ * n_grid hyperparameter points grid[3 g .. 3 g + 2] = (l_1, l_2, s2) (one CTA each,
+ * Cholesky in binary64 on the device), keeps the best (lml[n_grid] and *best, either
+ * may be NULL) and alpha = K^-1 y there.  Inputs may be host or device memory.
+ * Synchronises. */
+#define DSMC_GP_MAX_POINTS 128
+typedef struct dsmc_gp* dsmc_gp_handle;
+DSMC_API dsmc_status dsmc_gp_fit(const double* X, const double* Y, int n, int m,
+                                 const double* grid, int n_grid, void* stream,
+                                 dsmc_gp_handle* out, double* lml, int* best);
+/* Predictive means at ns points Xs (ns x 2) into out (ns x m).  Synchronises. */
+DSMC_API dsmc_status dsmc_gp_predict(dsmc_gp_handle gp, const double* Xs, int ns, double* out);
+DSMC_API dsmc_status dsmc_gp_hyper(dsmc_gp_handle gp, double* l1, double* l2, double* s2);
+DSMC_API dsmc_status dsmc_gp_destroy(dsmc_gp_handle gp);
+
+/* The cell-centred finite-volume solve of Eq. 8 on n cells with the stress correction
+ * S given at the n + 1 faces and the wall values of Eq. 9 (slip = 0) or Eq. 10 with
+ * coefficient sigma_p (slip = 1): u[n] (host or device).  Synchronises. */
+DSMC_API dsmc_status dsmc_cfd_faces(double Kn, double F, int n, int slip, double sigma_p,
+                                    const double* S_faces, double* u, void* stream);
 
 /* Tuner of the step's work split.  For CTA shapes of 8 and 4 warps and span sizes
  * 1024, 2048, ... particles (those whose shared memory fits, skipping sizes that give

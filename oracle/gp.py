@@ -26,7 +26,7 @@ import numpy as np
 # Hyperparameter grid (length scales on the unit square, noise variance of
 # standardised outputs).
 GRID = [(l1, l2, s2) for l1 in (0.05, 0.1, 0.2, 0.4, 0.8) for l2 in (0.25, 1.0, 4.0)
-        for s2 in (1e-4, 1e-3, 1e-2, 1e-1)]
+        for s2 in (1e-4, 1e-3, 1e-2, 3e-2, 1e-1, 3e-1)]
 
 
 def kernel(A, B, l1: float, l2: float):

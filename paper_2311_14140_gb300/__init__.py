@@ -9,10 +9,10 @@ MMS hybrid (DSMC in the Knudsen layer, Chapman-Enskog interface, iterated CFD);
 ``fields`` turns raw moment sums into cell fields; ``workloads`` names the synthetic
 runs.  Build the library with ``__graft_entry__.build()`` or ``_build.build()``.
 """
-from .dsmc import (Dsmc, DsmcBatch, DsmcError, DsmcPool, Options, Surrogate,  # noqa: F401
-                   default_options, fields, load_library, mms_hybrid, solve,
-                   surrogate_exponents)
+from .dsmc import (Dsmc, DsmcBatch, DsmcError, DsmcPool, GaussianProcess, Options,  # noqa: F401
+                   Surrogate, cfd_faces, default_options, fields, load_library, mms_hybrid,
+                   solve, surrogate_exponents)
 
-__all__ = ["Dsmc", "DsmcBatch", "DsmcError", "DsmcPool", "Options", "Surrogate",
-           "default_options", "fields", "load_library", "mms_hybrid", "solve",
-           "surrogate_exponents"]
+__all__ = ["Dsmc", "DsmcBatch", "DsmcError", "DsmcPool", "GaussianProcess", "Options",
+           "Surrogate", "cfd_faces", "default_options", "fields", "load_library", "mms_hybrid",
+           "solve", "surrogate_exponents"]

@@ -215,6 +215,18 @@ __global__ void __launch_bounds__(128) k_trials(TrialModels tm, const double* __
   for (int i = n - 2; i >= 0; --i) ut[i] -= ct[i] * ut[i + 1];
 }
 
+// S(y) of Eq. 14 with weights w (k of them) at the faces y = f / n, f = 0..n.
+__global__ void k_correction(int k, double w0, double w1, double w2, double b0, double b1,
+                             double b2, int n, double* __restrict__ S) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f > n) return;
+  const double y = (double)f / n;
+  const double w[3] = {w0, w1, w2}, b[3] = {b0, b1, b2};
+  double s = 0.0;
+  for (int l = 0; l < k; ++l) s += w[l] * (exp(-b[l] * y) - exp(-b[l] * (1.0 - y)));
+  S[f] = s;
+}
+
 __global__ void k_bands(const double* __restrict__ u, int n_trials, int n,
                         double* __restrict__ mean, double* __restrict__ sd) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -574,6 +586,27 @@ dsmc_status dsmc_surrogate_train(dsmc_surrogate_handle s, dsmc_surrogate_fit* ou
   s->fit = f;
   s->fitted = true;
   *out = f;
+  return DSMC_OK;
+}
+
+dsmc_status dsmc_surrogate_correction(const dsmc_surrogate_fit* fit, int n, double* S_faces,
+                                      void* stream) {
+  if (!fit || !S_faces) return reject(DSMC_E_INVAL, "surrogate: NULL");
+  if (n < 1 || fit->sel_c < 0 || fit->sel_c > 3)
+    return reject(DSMC_E_INVAL, "surrogate: n >= 1 and a selected model in C0..C3");
+  cudaStream_t st = (cudaStream_t)stream;
+  double* d = nullptr;
+  SUR_CUDA(cudaMalloc(&d, ((size_t)n + 1) * sizeof(double)), "correction memory");
+  const int k = fit->sel_c;
+  const double* m = fit->m_c[k];
+  k_correction<<<(n + 1 + 127) / 128, 128, 0, st>>>(k, m[0], m[1], m[2], fit->b[0], fit->b[1],
+                                                    fit->b[2], n, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(S_faces, d, ((size_t)n + 1) * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_reject(e, "correction");
   return DSMC_OK;
 }
 

@@ -177,6 +177,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                             c.POINTER(RequestResult)]),
         "dsmc_device_moments_of": (st, [H, c.c_int, c.POINTER(c.c_void_p)]),
         "dsmc_set_open_top": (st, [H, c.c_int, c.c_double, c.c_double]),
+        "dsmc_gp_fit": (st, [c.c_void_p, c.c_void_p, c.c_int, c.c_int, c.c_void_p, c.c_int,
+                             c.c_void_p, c.POINTER(H), c.c_void_p, c.POINTER(c.c_int)]),
+        "dsmc_gp_predict": (st, [H, c.c_void_p, c.c_int, c.c_void_p]),
+        "dsmc_gp_hyper": (st, [H, c.POINTER(c.c_double), c.POINTER(c.c_double),
+                               c.POINTER(c.c_double)]),
+        "dsmc_gp_destroy": (st, [H]),
+        "dsmc_surrogate_correction": (st, [c.POINTER(SurrogateFit), c.c_int, c.c_void_p,
+                                           c.c_void_p]),
+        "dsmc_cfd_faces": (st, [c.c_double, c.c_double, c.c_int, c.c_int, c.c_double,
+                                c.c_void_p, c.c_void_p, c.c_void_p]),
         "dsmc_surrogate_create_region": (st, [c.c_double, c.c_double, c.c_int, c.c_int,
                                               c.c_double, c.c_int, c.c_void_p, c.c_void_p,
                                               c.POINTER(H)]),
@@ -758,6 +768,80 @@ def mms_hybrid(Kn: float, F: float, *, omega: float = 0.5, dy: float = 0.005, pp
             "L_d": r.L_d, "b": tuple(r.b), "samples": r.samples,
             "interface": [(r.u_interface[i], r.p_interface[i]) for i in range(k)],
             "fit": _fit_dict(r.fit)}
+
+
+def _default_stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except Exception:
+            stream = None
+    return int(stream) if stream else None
+
+
+class GaussianProcess:
+    """GP regression on the device (``dsmc_gp_*``): the benchmark's GP variant of the
+    surrogate stage.  X: (n, 2) inputs on the unit square; Y: (n, m) outputs; grid:
+    sequence of (l1, l2, s2)."""
+
+    def __init__(self, X, Y, grid, stream=None):
+        L = load_library()
+        self._lib = L
+        X = np.ascontiguousarray(X, np.float64)
+        Y = np.ascontiguousarray(Y, np.float64)
+        if Y.ndim == 1:
+            Y = Y[:, None].copy()
+        g = np.ascontiguousarray(np.asarray(grid, np.float64).reshape(-1, 3))
+        self.m = Y.shape[1]
+        self.lml = np.empty(len(g), np.float64)
+        best = ctypes.c_int()
+        h = ctypes.c_void_p()
+        _check(L.dsmc_gp_fit(_ptr(X), _ptr(Y), X.shape[0], self.m, _ptr(g), len(g),
+                             _default_stream(stream), ctypes.byref(h), _ptr(self.lml),
+                             ctypes.byref(best)))
+        self._h = h
+        self.best = best.value
+        v = [ctypes.c_double() for _ in range(3)]
+        _check(L.dsmc_gp_hyper(h, *[ctypes.byref(x) for x in v]))
+        self.hyper = tuple(x.value for x in v)
+
+    def predict(self, Xs):
+        Xs = np.ascontiguousarray(Xs, np.float64).reshape(-1, 2)
+        out = np.empty((Xs.shape[0], self.m), np.float64)
+        _check(self._lib.dsmc_gp_predict(self._h, _ptr(Xs), Xs.shape[0], _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dsmc_gp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cfd_faces(Kn: float, F: float, n: int, sigma_p, S_faces, stream=None):
+    """``dsmc_cfd_faces``: Eq. 8 on n cells with the stress correction at the faces;
+    sigma_p None means no slip."""
+    S = np.ascontiguousarray(S_faces, np.float64)
+    u = np.empty(int(n), np.float64)
+    _check(load_library().dsmc_cfd_faces(float(Kn), float(F), int(n), 0 if sigma_p is None else 1,
+                                         0.0 if sigma_p is None else float(sigma_p), _ptr(S),
+                                         _ptr(u), _default_stream(stream)))
+    return u
+
+
+def surrogate_correction(fit: dict, n: int, stream=None):
+    """S at the n + 1 faces of an n-cell grid for a fit's selected model."""
+    S = np.empty(int(n) + 1, np.float64)
+    _check(load_library().dsmc_surrogate_correction(ctypes.byref(fit["_raw"]), int(n), _ptr(S),
+                                                    _default_stream(stream)))
+    return S
 
 
 def surrogate_exponents(Kn: float):

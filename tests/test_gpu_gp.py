@@ -1,0 +1,78 @@
+"""The Gaussian-process variant of the surrogate stage (an item of the benchmark's
+configurations, not the paper's method) on the GPU: the device GP (binary64 Cholesky per
+hyperparameter point) against the oracle's on seeded data, the face-given CFD and the
+stress correction against the oracle's, and the whole variant: 64 DSMC runs at
+Latin-hypercube (Kn, force) points in one batch, the paper's surrogates per run, a GP over
+the design, and the corrected CFD against fresh DSMC at 8 held-out points."""
+import numpy as np
+import pytest
+
+from oracle import gp as GP
+from oracle import surrogate as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_14140_gb300 import _build
+    _build.build()
+
+
+def _data(seed, n=64, m=41):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(size=(n, 2))
+    K = GP.kernel(X, X, 0.3, 2.0) + 1e-8 * np.eye(n)
+    Y = np.linalg.cholesky(K) @ rng.normal(size=(n, m)) * np.linspace(0.1, 2, m)
+    Y += 0.05 * rng.normal(size=Y.shape) + np.linspace(-1, 3, m)
+    return X, Y
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gp_matches_oracle(seed):
+    from paper_2311_14140_gb300 import GaussianProcess
+    X, Y = _data(seed)
+    g = GaussianProcess(X, Y, GP.GRID)
+    o = GP.fit(X, Y)
+    np.testing.assert_allclose(g.lml, o["lml"], rtol=1e-9)
+    assert g.best == o["best"] and g.hyper == o["hyper"]
+    Xs = np.random.default_rng(50 + seed).uniform(size=(9, 2))
+    np.testing.assert_allclose(g.predict(Xs), GP.predict(o, Xs), rtol=1e-8,
+                               atol=1e-10 * np.abs(Y).max())
+
+
+def test_cfd_and_correction_match_oracle():
+    from paper_2311_14140_gb300 import cfd_faces
+    from paper_2311_14140_gb300.dsmc import surrogate_correction
+    Kn, F, n = 0.7, 3e-3, 200
+    b = S.exponents(Kn)
+    yf = np.arange(n + 1) / n
+    Sf = S.stress_correction(yf, (0.3, -0.1), b[:2])
+    np.testing.assert_allclose(cfd_faces(Kn, F, n, 1.2, Sf), GP.cfd_faces(Kn, F, n, 1.2, Sf),
+                               rtol=1e-11, atol=1e-16)
+    np.testing.assert_allclose(cfd_faces(Kn, F, n, None, Sf), GP.cfd_faces(Kn, F, n, None, Sf),
+                               rtol=1e-11, atol=1e-16)
+    fit = {"_raw": None}
+    from paper_2311_14140_gb300 import dsmc as D
+    raw = D.SurrogateFit()
+    raw.sel_c = 2
+    raw.m_c[2][0], raw.m_c[2][1] = 0.3, -0.1
+    for l in range(3):
+        raw.b[l] = b[l]
+    fit["_raw"] = raw
+    np.testing.assert_allclose(surrogate_correction(fit, n), Sf, rtol=1e-12, atol=1e-15)
+
+
+def test_gp_variant_predicts_held_out_dsmc():
+    import torch
+    from paper_2311_14140_gb300 import gp_variant as V
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        r = V.run(stream=s.cuda_stream)
+    errs = np.array(r["errors"])
+    # largest 10-bin difference relative to the held-out DSMC's peak velocity; the DSMC's
+    # own bin noise is 1-3 % at the lowest forces
+    assert errs.mean() < 0.05 and errs.max() < 0.10, errs
