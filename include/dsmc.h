@@ -97,6 +97,10 @@ typedef struct dsmc_options {
   int cta_warps;          /* warps per CTA of the collide/move pass: 0 keeps the shape
                              in use (8 at creation, or what dsmc_autotune chose), else 4
                              or 8; results are identical; default 0 */
+  int span_rows;          /* sort-matrix rows per span, one per equal part of its
+                             slots, each scattered by its own warp: 0 keeps the value
+                             in use (1 at creation, or what dsmc_autotune chose), else
+                             1 or 2; results are identical; default 0 */
   int graph;              /* 1: dsmc_step replays the launches of 16 steps as one
                              CUDA graph (captured on first use; needs a stream other
                              than the legacy default; off while profiling); results
@@ -125,6 +129,7 @@ typedef struct dsmc_info {
   int n_instances;     /* instances in the handle */
   int span_particles;  /* particles per span of the partition in use */
   int cta_warps;       /* warps per CTA of the collide/move pass in use */
+  int span_rows;       /* sort-matrix rows per span in use */
   int cells_per_span;  /* this instance's cells per span of the step passes */
   int n_spans;         /* this instance's spans (CTAs of the collide/move pass) */
   int total_spans;     /* spans of all instances */
@@ -526,10 +531,11 @@ DSMC_API dsmc_status dsmc_gp_destroy(dsmc_gp_handle gp);
 DSMC_API dsmc_status dsmc_cfd_faces(double Kn, double F, int n, int slip, double sigma_p,
                                     const double* S_faces, double* u, void* stream);
 
-/* Tuner of the step's work split.  For CTA shapes of 8 and 4 warps and span sizes
- * 1024, 2048, ... particles (those whose shared memory fits, skipping sizes that give
- * the same partition) it runs one untimed and steps_per_trial timed steps, keeps the
- * fastest, and stores it in the handle's options (cta_warps, span_particles).  The trial steps are real steps of the run: they
+/* Tuner of the step's work split.  For CTA shapes of 8 and 4 warps, 1 or 2 sort rows per
+ * span, and span sizes 1024, 2048, ... particles (those whose shared memory fits,
+ * skipping sizes that give the same partition) it runs one untimed and steps_per_trial
+ * timed steps, keeps the fastest, and stores it in the handle's options (cta_warps,
+ * span_rows, span_particles).  The trial steps are real steps of the run: they
  * advance every instance, and since the partition does not change results the run is
  * the same as without tuning.  *best_span_particles and *best_ms_per_step (either may
  * be NULL) get the choice and its time per step.  Synchronises. */

@@ -136,6 +136,8 @@ dsmc_status check_options(const dsmc_options* o) {
     return fail(DSMC_E_INVAL, "options: span_particles must be 0 or 1024..2^24");
   if (o->cta_warps != 0 && o->cta_warps != kAWarps && o->cta_warps != kAWarpsSmall)
     return fail(DSMC_E_INVAL, "options: cta_warps must be 0, 4 or 8");
+  if (o->span_rows < 0 || o->span_rows > kMaxSpanRows)
+    return fail(DSMC_E_INVAL, "options: span_rows must be 0, 1 or 2");
   if (o->graph && o->stream == nullptr)
     return fail(DSMC_E_INVAL, "options: graph replay needs a stream other than the legacy default");
   return DSMC_OK;
@@ -272,7 +274,7 @@ Capacity capacity_of(const dsmc_instance* d, int n) {
     C.slots += padded_slots(N);
     C.cells += d[i].n_cells;
     C.offs += d[i].n_cells + 1;
-    C.hist_ints += (long long)rows * d[i].n_cells;
+    C.hist_ints += (long long)rows * kMaxSpanRows * d[i].n_cells;
     C.spans += rows;
   }
   C.inst = n;
@@ -298,7 +300,7 @@ dsmc_status capacity_of_pool(const dsmc_pool_limits* lim, Capacity* C) {
   // An instance of N particles reserves at most N / 1024 + 1 sort-matrix rows.
   const long long rows = lim->max_particles / kMinSpanParticles + lim->max_instances;
   c.spans = (int)std::min<long long>(rows, INT_MAX / 2);
-  c.hist_ints = rows * (long long)lim->max_cells_per_instance;
+  c.hist_ints = rows * kMaxSpanRows * (long long)lim->max_cells_per_instance;
   *C = c;
   return DSMC_OK;
 }
@@ -336,6 +338,7 @@ struct dsmc_sim {
   long long gstep = 0;     // steps this handle has launched
   int span_target = kDefaultSpanParticles;
   int cta_warps = kAWarps;  // warps per CTA of the collide/move pass
+  int span_rows = 1;        // sort-matrix rows per span
   int spans = 0, max_cps = 1, max_cells = 1;  // partition in use
   int spans_reserved = 0;
   Capacity C{};
@@ -422,8 +425,8 @@ dsmc_status collect_times(dsmc_sim* h) {
 
 // The step passes must fit one CTA's shared memory with this partition, group size and
 // CTA shape.
-bool step_fits(int max_cells, int max_cps, int G, int warps = kAWarps) {
-  return step_smem_layout(max_cells, max_cps, G + G / 2 - 1, warps).total <= kStepSmemMax;
+bool step_fits(int max_cells, int max_cps, int G, int warps = kAWarps, int rows = 1) {
+  return step_smem_layout(max_cells, max_cps, G + G / 2 - 1, warps, rows).total <= kStepSmemMax;
 }
 
 // The largest cells-per-span any active instance (and `extra`, if given) would use
@@ -540,6 +543,7 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   L.max_cps = h->max_cps;
   L.max_cap = h->cap();
   L.warps = h->cta_warps;
+  L.rows = h->span_rows;
   L.gstep = h->gstep;
   L.gstep_dev = h->capturing ? h->gstep_dev : nullptr;
   L.count_only = count_only ? 1 : 0;
@@ -641,6 +645,7 @@ dsmc_status admit_fresh(dsmc_sim* h) {
   SL.max_cps = m;
   SL.max_cap = h->cap();
   SL.warps = h->cta_warps;
+  SL.rows = h->span_rows;
   SL.gstep = h->gstep;
   SL.gstep_dev = nullptr;
   SL.count_only = 1;
@@ -791,7 +796,7 @@ dsmc_status add_instance(dsmc_sim* h, const dsmc_instance& d, int index, int n_d
                                   "time step undefined: set options.dt for infinite Kn");
   int mcps, mcells;
   partition_extent(h, h->span_target, &x, &mcps, &mcells);
-  if (!step_fits(mcells, mcps, h->opt.group_size, h->cta_warps))
+  if (!step_fits(mcells, mcps, h->opt.group_size, h->cta_warps, h->span_rows))
     return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   // Find a free id and room in every array.
   int new_id = -1;
@@ -809,7 +814,8 @@ dsmc_status add_instance(dsmc_sim* h, const dsmc_instance& d, int index, int n_d
   const long long ps = h->ex_slots.alloc(x.slot_len);
   const long long cb = ps < 0 ? -1 : h->ex_cells.alloc(x.n_cells);
   const long long ob = cb < 0 ? -1 : h->ex_offs.alloc(x.n_cells + 1);
-  const long long hb = ob < 0 ? -1 : h->ex_hist.alloc((long long)x.max_spans * x.n_cells);
+  const long long hb =
+      ob < 0 ? -1 : h->ex_hist.alloc((long long)x.max_spans * kMaxSpanRows * x.n_cells);
   if (hb < 0) {
     if (ob >= 0) h->ex_offs.release(ob, x.n_cells + 1);
     if (cb >= 0) h->ex_cells.release(cb, x.n_cells);
@@ -846,6 +852,7 @@ dsmc_status new_handle(const Capacity& C, const dsmc_options& opt, bool pool, vo
   h->L = layout_of(C);
   h->span_target = opt.span_particles ? opt.span_particles : kDefaultSpanParticles;
   h->cta_warps = opt.cta_warps ? opt.cta_warps : kAWarps;
+  h->span_rows = opt.span_rows ? opt.span_rows : 1;
   h->ex_slots.reset(C.slots);
   h->ex_cells.reset(C.cells);
   h->ex_offs.reset(C.offs);
@@ -941,7 +948,8 @@ dsmc_status create_run(const dsmc_instance* defs, int n_inst, const dsmc_options
       mcps = std::max(mcps, cps);
       mcells = std::max(mcells, defs[i].n_cells);
     }
-    if (!step_fits(mcells, mcps, opt.group_size, opt.cta_warps ? opt.cta_warps : kAWarps))
+    if (!step_fits(mcells, mcps, opt.group_size, opt.cta_warps ? opt.cta_warps : kAWarps,
+                   opt.span_rows ? opt.span_rows : 1))
       return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   }
   dsmc_sim* h = nullptr;
@@ -992,6 +1000,7 @@ dsmc_status dsmc_default_options(dsmc_options* opt) {
   opt->profile = 0;
   opt->span_particles = 0;
   opt->cta_warps = 0;
+  opt->span_rows = 0;
   opt->graph = 0;
   opt->stream = nullptr;
   return DSMC_OK;
@@ -1079,7 +1088,7 @@ dsmc_status dsmc_pool_remove(dsmc_handle h, int id) {
   h->ex_slots.release(x.part_base, x.slot_len);
   h->ex_cells.release(x.cell_base, x.n_cells);
   h->ex_offs.release(x.off_base, x.n_cells + 1);
-  h->ex_hist.release(x.hist_base, (long long)x.max_spans * x.n_cells);
+  h->ex_hist.release(x.hist_base, (long long)x.max_spans * kMaxSpanRows * x.n_cells);
   h->spans_reserved -= x.max_spans;
   x.active = false;
   x.fresh = false;
@@ -1151,9 +1160,10 @@ dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt) {
   // span_particles = 0 and cta_warps = 0 keep the partition and CTA shape in use.
   const int target_use = opt->span_particles ? opt->span_particles : h->span_target;
   const int warps_use = opt->cta_warps ? opt->cta_warps : h->cta_warps;
+  const int rows_use = opt->span_rows ? opt->span_rows : h->span_rows;
   int mcps, mcells;
   partition_extent(h, target_use, nullptr, &mcps, &mcells);
-  if (!step_fits(mcells, mcps, opt->group_size, warps_use))
+  if (!step_fits(mcells, mcps, opt->group_size, warps_use, rows_use))
     return fail(DSMC_E_INVAL, "n_cells and group_size exceed the step's shared memory");
   if (h->events_used) {
     s = collect_times(h);
@@ -1162,6 +1172,7 @@ dsmc_status dsmc_set_options(dsmc_handle h, const dsmc_options* opt) {
   h->opt = *opt;
   for (int id : h->order) h->inst[id].p = ps[id];
   h->cta_warps = warps_use;
+  h->span_rows = rows_use;
   if (target_use != h->span_target) set_partition(h, target_use);
   h->tab_dirty = true;
   drop_graph(h);  // launch shapes or the stream may have changed
@@ -1195,16 +1206,17 @@ dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_par
     cudaEventDestroy(e0);
     return fail(DSMC_E_CUDA, "event");
   }
-  int best = h->span_target, best_warps = h->cta_warps;
+  int best = h->span_target, best_warps = h->cta_warps, best_rows = h->span_rows;
   double best_ms = -1.0;
   dsmc_status r = DSMC_OK;
-  const int shapes[2] = {kAWarps, kAWarpsSmall};
-  for (int w : shapes) {
+  const int shapes[4][2] = {{kAWarps, 1}, {kAWarps, 2}, {kAWarpsSmall, 1}, {kAWarpsSmall, 2}};
+  for (const auto& shape : shapes) {
+    const int w = shape[0], rows = shape[1];
     long long last_sig = -1;
     for (int target = kMinSpanParticles; target <= (1 << 17) && r == DSMC_OK; target *= 2) {
       int mcps, mcells;
       partition_extent(h, target, nullptr, &mcps, &mcells);
-      if (!step_fits(mcells, mcps, h->opt.group_size, w)) break;
+      if (!step_fits(mcells, mcps, h->opt.group_size, w, rows)) break;
       // Skip targets that give the same partition as the last one.
       long long sig = 0;
       for (int id : h->order) {
@@ -1215,6 +1227,7 @@ dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_par
       if (sig == last_sig) continue;
       last_sig = sig;
       h->cta_warps = w;
+      h->span_rows = rows;
       set_partition(h, target);
       // one untimed step with the new shape, then the timed trial
       if ((r = step_n(h, 1)) != DSMC_OK) break;
@@ -1229,6 +1242,7 @@ dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_par
         best_ms = per;
         best = target;
         best_warps = w;
+        best_rows = rows;
       }
     }
     if (r != DSMC_OK) break;
@@ -1237,9 +1251,11 @@ dsmc_status dsmc_autotune(dsmc_handle h, int steps_per_trial, int* best_span_par
   cudaEventDestroy(e1);
   if (r != DSMC_OK) return r;
   h->cta_warps = best_warps;
+  h->span_rows = best_rows;
   set_partition(h, best);
   h->opt.span_particles = best;
   h->opt.cta_warps = best_warps;
+  h->opt.span_rows = best_rows;
   if (best_span_particles) *best_span_particles = best;
   if (best_ms_per_step) *best_ms_per_step = best_ms;
   if (h->opt.profile) return collect_times(h);
@@ -1443,6 +1459,7 @@ dsmc_status dsmc_get_info_of(dsmc_handle h, int id, dsmc_info* info) {
   info->n_instances = h->n_inst();
   info->span_particles = h->span_target;
   info->cta_warps = h->cta_warps;
+  info->span_rows = h->span_rows;
   info->cells_per_span = x.cps;
   info->n_spans = x.n_spans;
   info->total_spans = h->spans;

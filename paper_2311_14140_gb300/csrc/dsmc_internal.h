@@ -12,6 +12,7 @@ constexpr int kNMom = 13;          // raw moment sums per cell
 constexpr int kMaxGroup = 512;     // largest collision group size G
 constexpr int kAWarps = 8;         // warps per CTA of the collide/move pass (default)
 constexpr int kAWarpsSmall = 4;    // the other CTA shape the tuner may choose
+constexpr int kMaxSpanRows = 2;    // rows of the sort matrix per span (halves of its slots)
 constexpr int kBWarpsMax = 4;      // warps (spans) per CTA of the span scatter
 constexpr int kMaxStepCells = 16384;
 constexpr int kMaxSpans = 152 * 16;   // rows of the per-step sort matrix, at most
@@ -109,11 +110,11 @@ struct StepSmem {
 __host__ __device__ inline size_t step_align(size_t o, size_t a) { return (o + a - 1) / a * a; }
 
 __host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int cap,
-                                                     int warps = kAWarps) {
+                                                     int warps = kAWarps, int rows = 1) {
   StepSmem L;
   size_t o = 0;
   L.hist = o;
-  o = step_align(o + (size_t)n_cells * 4, 8);
+  o = step_align(o + (size_t)rows * n_cells * 4, 8);
   L.cell_acc = o;
   o += (size_t)cps * kNMom * 8;
   L.cell_cand = o;
@@ -168,6 +169,9 @@ struct StepLaunch {
   int max_cps;
   int max_cap;
   int warps;             // warps per CTA of the collide/move pass (kAWarps or kAWarpsSmall)
+  int rows;              // sort-matrix rows per span, 1 or kMaxSpanRows: row r counts the
+                         // particles of the r-th half of the span's slots, and the scatter
+                         // gives each row its own warp
   long long gstep;       // global step number
   long long* gstep_dev;  // non-NULL (graph replay): read the step number here instead;
                          // the cell-offset kernel advances it at the end of the step

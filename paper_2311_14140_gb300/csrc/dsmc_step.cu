@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
   const int cps = a.cps;
   const int cap = a.cap;
   const int G = a.G;
-  const StepSmem L = step_smem_layout(n_cells, cps, cap, kWarps);
+  const int R = SL.rows;
+  const StepSmem L = step_smem_layout(n_cells, cps, cap, kWarps, R);
   int* h = reinterpret_cast<int*>(smem + L.hist);
   double* cacc = reinterpret_cast<double*>(smem + L.cell_acc);
   unsigned long long* ccand = reinterpret_cast<unsigned long long*>(smem + L.cell_cand);
@@ -239,16 +240,18 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
   const int c0 = span * cps;
   const int c1 = min(c0 + cps, n_cells);
   const unsigned lt = (1u << lane) - 1u;
-  int* row = hist + a.hist_base + (size_t)span * n_cells;
-  for (int i = threadIdx.x; i < n_cells; i += blockDim.x) h[i] = 0;
+  // rows (span R + r) of the sort matrix; row r counts the r-th half of the slots
+  int* row = hist + a.hist_base + (size_t)span * R * n_cells;
+  for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) h[i] = 0;
+  const int sb0 = off[c0], sb1 = off[c1];
+  const int mid = (R > 1) ? sb0 + ((sb1 - sb0) >> 1) : sb1;  // first slot of the second row
 
   if (count_only) {  // sort into cells: count the cells of the span's slots
     __syncthreads();
-    const int b0 = off[c0], b1 = off[c1];
-    for (int p = b0 + threadIdx.x; p < b1; p += blockDim.x)
-      atomicAdd(&h[cell_of(P[p].x, n_cells, a.ncf)], 1);
+    for (int p = sb0 + threadIdx.x; p < sb1; p += blockDim.x)
+      atomicAdd(&h[(p >= mid ? n_cells : 0) + cell_of(P[p].x, n_cells, a.ncf)], 1);
     __syncthreads();
-    for (int i = threadIdx.x; i < n_cells; i += blockDim.x) row[i] = h[i];
+    for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) row[i] = h[i];
     return;
   }
 
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
         if (!hits) {
           const float xx = fadd(r.y, fmul(a.F, a.dt));
           P[gs + i] = make_float4(ynew, xx, r.z, r.w);
-          atomicAdd(&h[cell_of(ynew, n_cells, a.ncf)], 1);
+          atomicAdd(&h[(gs + i >= mid ? n_cells : 0) + cell_of(ynew, n_cells, a.ncf)], 1);
         }
       }
       const unsigned q = __ballot_sync(kFull, hits);
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
                  a.open_top, a.u_top, a.p_top, inflow_fail))
           bad_bounce = true;
         P[p] = make_float4(yy, xx, uy, zz);
-        atomicAdd(&h[cell_of(yy, n_cells, a.ncf)], 1);
+        atomicAdd(&h[(p >= mid ? n_cells : 0) + cell_of(yy, n_cells, a.ncf)], 1);
       }
     }
     __syncwarp();
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
   if (inflow_fail) atomicOr(err, kErrInflow);
   __syncthreads();
 
-  for (int i = threadIdx.x; i < n_cells; i += blockDim.x) row[i] = h[i];
+  for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) row[i] = h[i];
   for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     const int lc = c - c0;
     const float gm = __uint_as_float(cgmax[lc]);
@@ -564,7 +567,9 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   extern __shared__ int sh_run[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int gspan = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int unit = blockIdx.x * (blockDim.x >> 5) + wib;  // (span, row of the span)
+  const int R = SL.rows;
+  const int gspan = unit / R, sub = unit - gspan * R;
   if (gspan >= SL.n_spans_total) return;
   const InstParams& a = instance_of<kBatch>(one, SL, gspan);
   const int n_cells = a.n_cells;
@@ -572,13 +577,15 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   const int* __restrict__ off_cur = off_cur_all + a.off_base;
   const int* __restrict__ off_new = off_new_all + a.off_base;
   int* run = sh_run + (size_t)wib * SL.max_cells;
-  const int* row = hist + a.hist_base + (size_t)span * n_cells;
+  const int* row = hist + a.hist_base + ((size_t)span * R + sub) * n_cells;
   for (int c = lane; c < n_cells; c += 32) run[c] = off_new[c] + row[c];
   __syncwarp();
   const int c0 = span * a.cps;
   const int c1 = min(c0 + a.cps, n_cells);
-  const int b0 = off_cur[c0];
-  const int b1 = off_cur[c1];
+  const int sb0 = off_cur[c0], sb1 = off_cur[c1];
+  const int mid = (R > 1) ? sb0 + ((sb1 - sb0) >> 1) : sb1;
+  const int b0 = (sub == 0) ? sb0 : mid;
+  const int b1 = (sub == 0) ? mid : sb1;
   const int lo = a.part_base, hi = a.part_base + a.n_part;  // the instance's slots
   const unsigned lt = (1u << lane) - 1u;
   bool bad = false;
@@ -605,7 +612,7 @@ __global__ void __launch_bounds__(1024)
   const InstParams& a = kBatch ? SL.tab[blockIdx.y] : one;
   const int n_cells = a.n_cells;
   if ((int)blockIdx.x * 32 >= n_cells) return;
-  const int n_rows = a.n_spans;
+  const int n_rows = a.n_spans * SL.rows;
   int* __restrict__ m = hist + a.hist_base;
   int* __restrict__ count = count_all + a.cell_base;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -780,7 +787,7 @@ cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 cudaStream_t st) {
   const bool small = L.warps == kAWarpsSmall;
   const int warps = small ? kAWarpsSmall : kAWarps;
-  const StepSmem S = step_smem_layout(L.max_cells, L.max_cps, L.max_cap, warps);
+  const StepSmem S = step_smem_layout(L.max_cells, L.max_cps, L.max_cap, warps, L.rows);
   const dim3 block(warps * 32);
 #define DSMC_COLLIDE(B, W)                                                                   \
   k_collide_move<B, W><<<L.n_spans_total, block, S.total, st>>>(P, off, smax_in, smax_out, \
@@ -812,7 +819,8 @@ cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur
                                  const StepLaunch& L, int* err, cudaStream_t st) {
   const int wpb = scatter_spans_warps(L.max_cells);
   const size_t smem = (size_t)wpb * L.max_cells * sizeof(int);
-  const int blocks = (L.n_spans_total + wpb - 1) / wpb;
+  const int units = L.n_spans_total * L.rows;
+  const int blocks = (units + wpb - 1) / wpb;
   if (L.n_inst == 1)
     k_scatter_spans<false><<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, one, L,
                                                           err);

@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("sample_start", ctypes.c_longlong), ("group_size", ctypes.c_int),
                 ("collisions", ctypes.c_int), ("profile", ctypes.c_int),
                 ("span_particles", ctypes.c_int), ("cta_warps", ctypes.c_int),
-                ("graph", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("span_rows", ctypes.c_int), ("graph", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -53,7 +54,8 @@ class Info(ctypes.Structure):
                 ("cvhs", ctypes.c_float), ("vexp", ctypes.c_float), ("vinv", ctypes.c_float), ("lncv", ctypes.c_float),
                 ("smax0", ctypes.c_float), ("device_bytes", ctypes.c_size_t),
                 ("n_instances", ctypes.c_int), ("span_particles", ctypes.c_int),
-                ("cta_warps", ctypes.c_int), ("cells_per_span", ctypes.c_int), ("n_spans", ctypes.c_int),
+                ("cta_warps", ctypes.c_int), ("span_rows", ctypes.c_int),
+                ("cells_per_span", ctypes.c_int), ("n_spans", ctypes.c_int),
                 ("total_spans", ctypes.c_int), ("first_slot", ctypes.c_int),
                 ("first_cell", ctypes.c_int)]
 
@@ -257,8 +259,9 @@ class Dsmc:
                  body_force: float = 0.0, seed: int = 0, wall_T: float = 273.0,
                  dt_factor: float = 0.2, dt: float = 0.0, sample_start: int = 0,
                  group_size: int = 256, collisions: bool = True, profile: bool = False,
-                 span_particles: int = 0, cta_warps: int = 0, graph: bool = False,
-                 stream=None, workspace: str = "torch", gas: Optional[dict] = None):
+                 span_particles: int = 0, cta_warps: int = 0, span_rows: int = 0,
+                 graph: bool = False, stream=None, workspace: str = "torch",
+                 gas: Optional[dict] = None):
         L = load_library()
         self._lib = L
         self.n_cells, self.ppc = int(n_cells), int(ppc)
@@ -270,6 +273,7 @@ class Dsmc:
         o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
         o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
         o.span_particles, o.cta_warps, o.graph = int(span_particles), int(cta_warps), int(bool(graph))
+        o.span_rows = int(span_rows)
         self._ws = None
         if workspace == "torch":
             import torch
@@ -400,11 +404,12 @@ def make_instance(Kn: float, n_cells: int, ppc: int, *, omega: float = 0.5,
 
 
 def _options(dt_factor=0.2, dt=0.0, sample_start=0, group_size=256, collisions=True,
-             profile=False, span_particles=0, cta_warps=0, graph=False) -> Options:
+             profile=False, span_particles=0, cta_warps=0, span_rows=0, graph=False) -> Options:
     o = default_options()
     o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
     o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
     o.span_particles, o.cta_warps, o.graph = int(span_particles), int(cta_warps), int(bool(graph))
+    o.span_rows = int(span_rows)
     return o
 
 
@@ -469,7 +474,9 @@ class _Multi:
         _check(self._lib.dsmc_autotune(self._h, int(steps_per_trial), ctypes.byref(best),
                                        ctypes.byref(ms)))
         self._opt.span_particles = best.value
-        self._opt.cta_warps = self.info(self._first_id())["cta_warps"]
+        inf = self.info(self._first_id())
+        self._opt.cta_warps = inf["cta_warps"]
+        self._opt.span_rows = inf["span_rows"]
         return best.value, ms.value
 
     def _first_id(self) -> int:

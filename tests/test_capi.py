@@ -44,7 +44,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_options(lib):
     o = D.default_options()
     assert (o.dt_factor, o.dt, o.sample_start, o.group_size, o.collisions, o.profile,
-            o.span_particles, o.cta_warps, o.graph) == (0.2, 0.0, 0, 256, 1, 0, 0, 0, 0)
+            o.span_particles, o.cta_warps, o.span_rows, o.graph) == \
+        (0.2, 0.0, 0, 256, 1, 0, 0, 0, 0, 0)
     assert lib.dsmc_kernel_count() == 7
     assert lib.dsmc_kernel_name(0) == b"init"
     assert lib.dsmc_status_string(4) == b"device limit reached"
@@ -86,7 +87,7 @@ def test_bad_gas_and_options_rejected(lib):
     assert st == 1 and "mass" in msg
     for field, val in (("group_size", 3), ("group_size", 1024), ("dt_factor", 0.0),
                        ("dt", -1.0), ("span_particles", 1000), ("span_particles", 1 << 25),
-                       ("cta_warps", 6), ("cta_warps", 16), ("graph", 1)):
+                       ("cta_warps", 6), ("cta_warps", 16), ("span_rows", 3), ("graph", 1)):
         o = D.default_options()
         setattr(o, field, val)
         st, msg = _create(lib, opt=o)

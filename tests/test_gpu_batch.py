@@ -127,15 +127,16 @@ def test_moments_all_is_the_concatenation():
         assert ns[i] == n == 6
 
 
-@pytest.mark.parametrize("span,warps", [(1024, 8), (4096, 4), (65536, 8), (2048, 4)])
-def test_partition_does_not_change_results(span, warps):
+@pytest.mark.parametrize("span,warps,rows", [(1024, 8, 1), (4096, 4, 2), (65536, 8, 2),
+                                             (2048, 4, 1)])
+def test_partition_does_not_change_results(span, warps, rows):
     ref = batch(DEFS)
     ref.step(10)
-    b = batch(DEFS, span_particles=span, cta_warps=warps)
+    b = batch(DEFS, span_particles=span, cta_warps=warps, span_rows=rows)
     b.step(4)
-    b.set_options(span_particles=2048, cta_warps=12 - warps)
+    b.set_options(span_particles=2048, cta_warps=12 - warps, span_rows=3 - rows)
     b.step(3)
-    b.set_options(span_particles=span, cta_warps=warps)
+    b.set_options(span_particles=span, cta_warps=warps, span_rows=rows)
     b.step(3)
     for i in range(len(DEFS)):
         assert_same_run(Member(ref, i), Member(b, i))

@@ -100,13 +100,13 @@ def test_hard_sphere_kn1_deterministic(steps):
     assert_bitexact(o, g)
 
 
-@pytest.mark.parametrize("warps", [8, 4])
-def test_vhs_kn01_multigroup_deterministic(warps):
+@pytest.mark.parametrize("warps,rows", [(8, 1), (4, 1), (8, 2)])
+def test_vhs_kn01_multigroup_deterministic(warps, rows):
     """VHS omega = 0.81 at Kn = 0.1 with 700 particles per cell: 2 or 3 collision groups
     per cell (group size 256, remainder merge), 20 steps, in both CTA shapes."""
     w = W.VHS_KN01_50M
     o, g = make_pair(omega=w.omega, Kn=w.Kn, n_cells=40, ppc=700, F=w.body_force, seed=3,
-                     cta_warps=warps)
+                     cta_warps=warps, span_rows=rows)
     o.step(20)
     g.step(20)
     assert_bitexact(o, g)
