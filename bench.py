@@ -78,11 +78,15 @@ def ncu_traffic(kernel: str):
     return None if k is None else k.get("dram_bytes_per_launch_full_size")
 
 
+# Sources of the step kernels the committed traffic figures were taken from.
+STEP_SOURCES = ("dsmc_step.cu", "dsmc_device.cuh", "dsmc_internal.h")
+
+
 def sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_14140_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in STEP_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode() + b"\0" + f.read())
     return h.hexdigest()

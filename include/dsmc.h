@@ -504,17 +504,16 @@ DSMC_API dsmc_status dsmc_mms_run(const dsmc_mms_params* p, void* stream, double
                                   const double* z, int n_trials, double* band_sd,
                                   dsmc_mms_result* out);
 
-/* Gaussian-process variant of the surrogate stage (an item of the benchmark's
- * configurations, not the paper's method): GP regression (Rasmussen and Williams 2006,
- * Ch. 2) over n <= DSMC_GP_MAX_POINTS design points X (n x 2, row-major, inputs scaled
- * to the unit square) with m output columns Y (n x m, row-major), squared-exponential
- * covariance exp(-1/2 ((dx_1 / l_1)^2 + (dx_2 / l_2)^2)) plus noise s2 on the diagonal,
- * each column standardised (mean, population standard deviation) and sharing the
- * covariance.  dsmc_gp_fit evaluates the summed log marginal likelihood at each of
- * n_grid hyperparameter points grid[3 g .. 3 g + 2] = (l_1, l_2, s2) (one CTA each,
- * Cholesky in binary64 on the device), keeps the best (lml[n_grid] and *best, either
- * may be NULL) and alpha = K^-1 y there.  Inputs may be host or device memory.
- * Synchronises. */
+/* Gaussian-process variant of the surrogate stage (not the paper's method): GP
+ * regression (Rasmussen and Williams 2006, Ch. 2) over n <= DSMC_GP_MAX_POINTS design
+ * points X (n x 2, row-major, inputs scaled to the unit square) with m output columns Y
+ * (n x m, row-major), squared-exponential covariance
+ * exp(-1/2 ((dx_1 / l_1)^2 + (dx_2 / l_2)^2)) plus noise s2 on the diagonal, each column
+ * standardised (mean, population standard deviation) and sharing the covariance.
+ * dsmc_gp_fit evaluates the summed log marginal likelihood at each of n_grid
+ * hyperparameter points grid[3 g .. 3 g + 2] = (l_1, l_2, s2) (one CTA each, Cholesky in
+ * binary64 on the device), keeps the best (lml[n_grid] and *best, either may be NULL)
+ * and alpha = K^-1 y there.  Inputs may be host or device memory.  Synchronises. */
 #define DSMC_GP_MAX_POINTS 128
 typedef struct dsmc_gp* dsmc_gp_handle;
 DSMC_API dsmc_status dsmc_gp_fit(const double* X, const double* Y, int n, int m,

@@ -1,6 +1,5 @@
-"""Oracle of the Gaussian-process variant of the surrogate stage (an item of the
-benchmark's configurations, not of the paper, which uses Bayesian ridge regression per
-flow case): a GP over the (Kn, force) design of many DSMC runs predicts the slip
+"""Oracle of the Gaussian-process variant of the surrogate stage (not the paper's method,
+which uses Bayesian ridge regression per flow case): a GP over the (Kn, force) design of many DSMC runs predicts the slip
 coefficient and the stress correction of a new case, and the 1D CFD uses them.
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU baseline of the

@@ -1,8 +1,7 @@
-// dsmc_gp.cu -- the Gaussian-process variant of the surrogate stage, an item of the
-// benchmark's configurations rather than of the paper (whose surrogates are Bayesian
-// ridge regressions per flow case, Sec. 2.3): a GP over the (Kn, force) design of many
-// DSMC runs predicts the slip coefficient and the stress correction of a new case, and
-// the 1D CFD (Eq. 8 with Eq. 10) uses them.
+// dsmc_gp.cu -- a Gaussian-process variant of the surrogate stage, not the paper's
+// method (whose surrogates are Bayesian ridge regressions per flow case, Sec. 2.3): a GP
+// over the (Kn, force) design of many DSMC runs predicts the slip coefficient and the
+// stress correction of a new case, and the 1D CFD (Eq. 8 with Eq. 10) uses them.
 //
 // GP regression as in Rasmussen and Williams (2006), Ch. 2 and Sec. 5.4: squared-
 // exponential covariance exp(-1/2 sum_d ((x_d - x'_d) / l_d)^2) over two inputs scaled to

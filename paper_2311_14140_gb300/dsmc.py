@@ -789,8 +789,8 @@ def _default_stream(stream):
 
 
 class GaussianProcess:
-    """GP regression on the device (``dsmc_gp_*``): the benchmark's GP variant of the
-    surrogate stage.  X: (n, 2) inputs on the unit square; Y: (n, m) outputs; grid:
+    """GP regression on the device (``dsmc_gp_*``): the GP variant of the surrogate stage
+    (not the paper's method).  X: (n, 2) inputs on the unit square; Y: (n, m) outputs; grid:
     sequence of (l1, l2, s2)."""
 
     def __init__(self, X, Y, grid, stream=None):

@@ -1,6 +1,7 @@
-"""The benchmark's Gaussian-process variant of the surrogate stage (not the paper's
-method): DSMC runs at Latin-hypercube (Kn, force) points, all advanced in one batch;
-each run's windows train the paper's Bayesian ridge regression surrogates
+"""A Gaussian-process variant of the surrogate stage (not the paper's method, which
+trains Bayesian ridge regressions per flow case): DSMC runs at Latin-hypercube
+(Kn, force) points, all advanced in one batch; each run's windows train the paper's
+Bayesian ridge regression surrogates
 (``Surrogate``); a GP over the design (``GaussianProcess``) learns each run's slip
 coefficient and its stress correction divided by F at the CFD faces; for a new (Kn, F)
 the CFD (``cfd_faces``) uses the GP's predictions.  Orchestration only: the DSMC, the

@@ -140,8 +140,8 @@ def latin_hypercube(n: int, dims: int = 2, seed: int = 0):
     return u
 
 
-# Range of the Gaussian-process variant's design (an item of the benchmark, not of the
-# paper): Kn log-uniform over the paper's verification range 0.1-5 (Sec. 3.1) and a
+# Range of the Gaussian-process variant's design (the variant is not the paper's
+# method): Kn log-uniform over the paper's verification range 0.1-5 (Sec. 3.1) and a
 # force factor in [0.5, 2] times F_ma(Kn), the force whose slip-Stokes channel-mean
 # speed is 0.02 v0 (Ma ~ 0.02).
 GP_KN = (0.1, 5.0)

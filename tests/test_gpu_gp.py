@@ -1,5 +1,5 @@
-"""The Gaussian-process variant of the surrogate stage (an item of the benchmark's
-configurations, not the paper's method) on the GPU: the device GP (binary64 Cholesky per
+"""The Gaussian-process variant of the surrogate stage (not the paper's method) on the
+GPU: the device GP (binary64 Cholesky per
 hyperparameter point) against the oracle's on seeded data, the face-given CFD and the
 stress correction against the oracle's, and the whole variant: 64 DSMC runs at
 Latin-hypercube (Kn, force) points in one batch, the paper's surrogates per run, a GP over
