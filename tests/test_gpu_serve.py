@@ -93,16 +93,24 @@ def test_channel_sums_are_the_cell_sums():
         np.testing.assert_allclose(cs[i, 1], m[:, 1].sum(), rtol=1e-12, atol=1e-9)
 
 
-def test_serve_results_equal_the_same_runs_alone():
+@pytest.mark.parametrize("graph", [False, True])
+def test_serve_results_equal_the_same_runs_alone(graph):
     """Six requests arriving at once into a pool that holds three of them at a time,
     each to a 30 % standard error (capped at 640 steps); every result is then replayed
-    as a run of its own for the steps the loop reports."""
+    as a run of its own for the steps the loop reports.  With graph replay the pool's
+    membership changes between replays (admissions and removals invalidate the graph)."""
+    import torch
     defs = [A, B, C, D_, dict(A, seed=5, Kn=2.0), dict(C, seed=9, n_cells=80)]
     reqs = [dict(d, arrival=0.0, target_se=0.3, max_steps=640) for d in defs]
     from paper_2311_14140_gb300 import DsmcPool
-    p = DsmcPool(max_particles=60_000, max_cells=1000, max_instances=8,
-                 max_cells_per_instance=400, sample_start=8)
-    res = p.serve(reqs, epoch_steps=16, batches=4)
+    # graph capture needs a stream other than the legacy default one
+    stream = torch.cuda.Stream() if graph else torch.cuda.current_stream()
+    kw = dict(graph=True, stream=stream.cuda_stream) if graph else {}
+    with torch.cuda.stream(stream):
+        p = DsmcPool(max_particles=60_000, max_cells=1000, max_instances=8,
+                     max_cells_per_instance=400, sample_start=8, **kw)
+        res = p.serve(reqs, epoch_steps=16, batches=4)
+        stream.synchronize()
     assert p.size() == 0
     for r, d in zip(res, defs):
         assert r["converged"] in (0, 1) and r["finished"] >= r["admitted"] >= 0.0
