@@ -515,9 +515,19 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
 // One warp per span: stable scatter of the span's records into the other buffer.  Slots
 // are taken 256 at a time (8 per lane); the loads of the next 256 are issued before the
 // current ones are placed, so each lane keeps 8 to 16 records in flight.
+//
+// A record's place is its cell's running slot (run[]) plus the number of lanes before
+// it in its 32-record slice that go to the same cell.  Those "peer" lanes come from a
+// small per-warp table of lane masks: each lane ORs its bit into entry (cell mod 256)
+// and reads the entry back.  While a slice's cells lie within 256 consecutive values,
+// which holds unless a particle crosses more than 255 cells in one step, two cells never
+// share an entry and the mask is exactly the set of same-cell lanes; otherwise the slice
+// falls back to __match_any_sync.  The table costs a few shared-memory operations per
+// slice, where __match_any_sync on ~25 distinct values of 32 was the scatter's bottleneck.
 namespace {
 
 constexpr int kScatterUnroll = 8;
+constexpr int kMaskSlots = 256;  // entries of the per-warp mask table (a power of two)
 
 __device__ __forceinline__ void load_batch(float4 (&r)[kScatterUnroll],
                                            const float4* __restrict__ P, int base, int b1,
@@ -530,24 +540,51 @@ __device__ __forceinline__ void load_batch(float4 (&r)[kScatterUnroll],
 }
 
 __device__ __forceinline__ bool place_batch(const float4 (&r)[kScatterUnroll],
-                                            float4* __restrict__ P2, int* run, int base, int b1,
+                                            float4* __restrict__ P2, int* run, unsigned* msk,
+                                            int base, int b1,
                                             int n_cells, float ncf, int lo, int hi, int lane,
                                             unsigned lt) {
-  bool bad = false;
+  int cell[kScatterUnroll];
+  unsigned peers[kScatterUnroll];
 #pragma unroll
   for (int u = 0; u < kScatterUnroll; ++u) {
     const int p = base + u * 32 + lane;
-    const bool act = p < b1;
-    const int cell = act ? cell_of(r[u].x, n_cells, ncf) : -1;
-    const unsigned peers = __match_any_sync(kFull, cell);
-    const int first = act ? run[cell] : 0;
+    cell[u] = (p < b1) ? cell_of(r[u].x, n_cells, ncf) : -1;  // -1: no record
+  }
+  // lanes of each slice bound for the same cell
+#pragma unroll
+  for (int u = 0; u < kScatterUnroll; ++u) {
+    const int cmin = __reduce_min_sync(kFull, cell[u] >= 0 ? cell[u] : INT_MAX);
+    const int cmax = __reduce_max_sync(kFull, cell[u]);
+    if (cmax - cmin < kMaskSlots) {  // no two cells share a slot of the mask table
+      const int slot = cell[u] & (kMaskSlots - 1);
+      if (cell[u] >= 0) atomicOr(&msk[slot], 1u << lane);
+      __syncwarp();
+      peers[u] = (cell[u] >= 0) ? msk[slot] : 0u;
+      __syncwarp();
+      if (cell[u] >= 0) msk[slot] = 0u;  // the table is all zero between slices
+      __syncwarp();
+    } else {
+      peers[u] = __match_any_sync(kFull, cell[u]);
+    }
+  }
+  // slots, slice after slice: the first lane of each peer group advances the run
+  int d[kScatterUnroll];
+#pragma unroll
+  for (int u = 0; u < kScatterUnroll; ++u) {
+    const bool act = cell[u] >= 0;
+    const int first = act ? run[cell[u]] : 0;
     __syncwarp();
-    if (act && (peers & lt) == 0) run[cell] = first + __popc(peers);
+    if (act && (peers[u] & lt) == 0) run[cell[u]] = first + __popc(peers[u]);
     __syncwarp();
-    if (act) {
-      const int d = first + __popc(peers & lt);
-      if (d >= lo && d < hi)
-        P2[d] = r[u];
+    d[u] = first + __popc(peers[u] & lt);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < kScatterUnroll; ++u) {
+    if (cell[u] >= 0) {
+      if (d[u] >= lo && d[u] < hi)
+        P2[d[u]] = r[u];
       else
         bad = true;
     }
@@ -576,7 +613,9 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   const int span = gspan - a.span_base;
   const int* __restrict__ off_cur = off_cur_all + a.off_base;
   const int* __restrict__ off_new = off_new_all + a.off_base;
-  int* run = sh_run + (size_t)wib * SL.max_cells;
+  int* run = sh_run + (size_t)wib * (SL.max_cells + kMaskSlots);
+  unsigned* msk = reinterpret_cast<unsigned*>(run + SL.max_cells);
+  for (int i = lane; i < kMaskSlots; i += 32) msk[i] = 0u;
   const int* row = hist + a.hist_base + ((size_t)span * R + sub) * n_cells;
   for (int c = lane; c < n_cells; c += 32) run[c] = off_new[c] + row[c];
   __syncwarp();
@@ -593,10 +632,10 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   load_batch(ra, P, b0, b1, lane);
   for (int base = b0; base < b1; base += 2 * kBatch2) {
     load_batch(rb, P, base + kBatch2, b1, lane);
-    bad |= place_batch(ra, P2, run, base, b1, n_cells, a.ncf, lo, hi, lane, lt);
+    bad |= place_batch(ra, P2, run, msk, base, b1, n_cells, a.ncf, lo, hi, lane, lt);
     if (base + kBatch2 >= b1) break;
     load_batch(ra, P, base + 2 * kBatch2, b1, lane);
-    bad |= place_batch(rb, P2, run, base + kBatch2, b1, n_cells, a.ncf, lo, hi, lane, lt);
+    bad |= place_batch(rb, P2, run, msk, base + kBatch2, b1, n_cells, a.ncf, lo, hi, lane, lt);
   }
   if (bad) atomicOr(err, kErrSort);
 }
@@ -809,7 +848,7 @@ cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
 }
 
 int scatter_spans_warps(int n_cells) {
-  size_t w = kStepSmemMax / ((size_t)n_cells * sizeof(int));
+  size_t w = kStepSmemMax / ((size_t)(n_cells + kMaskSlots) * sizeof(int));
   if (w > (size_t)kBWarpsMax) w = kBWarpsMax;
   return w < 1 ? 1 : (int)w;
 }
@@ -818,7 +857,7 @@ cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur
                                  const int* off_new, const int* hist, const InstParams& one,
                                  const StepLaunch& L, int* err, cudaStream_t st) {
   const int wpb = scatter_spans_warps(L.max_cells);
-  const size_t smem = (size_t)wpb * L.max_cells * sizeof(int);
+  const size_t smem = (size_t)wpb * (L.max_cells + kMaskSlots) * sizeof(int);
   const int units = L.n_spans_total * L.rows;
   const int blocks = (units + wpb - 1) / wpb;
   if (L.n_inst == 1)
