@@ -523,11 +523,15 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
 // which holds unless a particle crosses more than 255 cells in one step, two cells never
 // share an entry and the mask is exactly the set of same-cell lanes; otherwise the slice
 // falls back to __match_any_sync.  The table costs a few shared-memory operations per
-// slice, where __match_any_sync on ~25 distinct values of 32 was the scatter's bottleneck.
+// slice, where __match_any_sync on ~25 distinct values of 32 (2,000 cells, particles
+// crossing ~20 cells a step) was the scatter's bottleneck.  With few warps per SM the
+// longer chain of one warp matters more, and the launcher keeps __match_any_sync
+// (place_batch_match); both give the same places.
 namespace {
 
 constexpr int kScatterUnroll = 8;
 constexpr int kMaskSlots = 256;  // entries of the per-warp mask table (a power of two)
+constexpr int kMaskWarpsPerSm = 4;
 
 __device__ __forceinline__ void load_batch(float4 (&r)[kScatterUnroll],
                                            const float4* __restrict__ P, int base, int b1,
@@ -539,7 +543,7 @@ __device__ __forceinline__ void load_batch(float4 (&r)[kScatterUnroll],
   }
 }
 
-__device__ __forceinline__ bool place_batch(const float4 (&r)[kScatterUnroll],
+__device__ __forceinline__ bool place_batch_mask(const float4 (&r)[kScatterUnroll],
                                             float4* __restrict__ P2, int* run, unsigned* msk,
                                             int base, int b1,
                                             int n_cells, float ncf, int lo, int hi, int lane,
@@ -592,9 +596,37 @@ __device__ __forceinline__ bool place_batch(const float4 (&r)[kScatterUnroll],
   return bad;
 }
 
+// Ranking with __match_any_sync, slice after slice (fewer instructions in the chain of
+// one warp: the better choice when few warps share an SM).
+__device__ __forceinline__ bool place_batch_match(const float4 (&r)[kScatterUnroll],
+                                                  float4* __restrict__ P2, int* run, int base,
+                                                  int b1, int n_cells, float ncf, int lo, int hi,
+                                                  int lane, unsigned lt) {
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < kScatterUnroll; ++u) {
+    const int p = base + u * 32 + lane;
+    const bool act = p < b1;
+    const int cell = act ? cell_of(r[u].x, n_cells, ncf) : -1;
+    const unsigned peers = __match_any_sync(kFull, cell);
+    const int first = act ? run[cell] : 0;
+    __syncwarp();
+    if (act && (peers & lt) == 0) run[cell] = first + __popc(peers);
+    __syncwarp();
+    if (act) {
+      const int d = first + __popc(peers & lt);
+      if (d >= lo && d < hi)
+        P2[d] = r[u];
+      else
+        bad = true;
+    }
+  }
+  return bad;
+}
+
 }  // namespace
 
-template <bool kBatch>
+template <bool kBatch, bool kMask>
 __global__ void __launch_bounds__(kBWarpsMax * 32)
     k_scatter_spans(const float4* __restrict__ P, float4* __restrict__ P2,
                     const int* __restrict__ off_cur_all, const int* __restrict__ off_new_all,
@@ -632,10 +664,14 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   load_batch(ra, P, b0, b1, lane);
   for (int base = b0; base < b1; base += 2 * kBatch2) {
     load_batch(rb, P, base + kBatch2, b1, lane);
-    bad |= place_batch(ra, P2, run, msk, base, b1, n_cells, a.ncf, lo, hi, lane, lt);
+    bad |= kMask ? place_batch_mask(ra, P2, run, msk, base, b1, n_cells, a.ncf, lo, hi, lane, lt)
+                 : place_batch_match(ra, P2, run, base, b1, n_cells, a.ncf, lo, hi, lane, lt);
     if (base + kBatch2 >= b1) break;
     load_batch(ra, P, base + 2 * kBatch2, b1, lane);
-    bad |= place_batch(rb, P2, run, msk, base + kBatch2, b1, n_cells, a.ncf, lo, hi, lane, lt);
+    bad |= kMask ? place_batch_mask(rb, P2, run, msk, base + kBatch2, b1, n_cells, a.ncf, lo, hi,
+                                    lane, lt)
+                 : place_batch_match(rb, P2, run, base + kBatch2, b1, n_cells, a.ncf, lo, hi,
+                                     lane, lt);
   }
   if (bad) atomicOr(err, kErrSort);
 }
@@ -860,12 +896,27 @@ cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur
   const size_t smem = (size_t)wpb * (L.max_cells + kMaskSlots) * sizeof(int);
   const int units = L.n_spans_total * L.rows;
   const int blocks = (units + wpb - 1) / wpb;
-  if (L.n_inst == 1)
-    k_scatter_spans<false><<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, one, L,
-                                                          err);
-  else
-    k_scatter_spans<true><<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, one, L,
-                                                         err);
+  // the mask-table ranking once at least kMaskWarpsPerSm scatter warps share an SM
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const bool mask = units >= kMaskWarpsPerSm * sms;
+#define DSMC_SCATTER(B, M)                                                                   \
+  k_scatter_spans<B, M><<<blocks, wpb * 32, smem, st>>>(P, P2, off_cur, off_new, hist, one, L, \
+                                                        err)
+  if (L.n_inst == 1) {
+    if (mask)
+      DSMC_SCATTER(false, true);
+    else
+      DSMC_SCATTER(false, false);
+  } else {
+    if (mask)
+      DSMC_SCATTER(true, true);
+    else
+      DSMC_SCATTER(true, false);
+  }
+#undef DSMC_SCATTER
   return cudaGetLastError();
 }
 
@@ -930,11 +981,16 @@ cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes) {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a_bytes);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = cudaFuncSetAttribute(k_scatter_spans<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_scatter_spans<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)b_bytes);
+  const void* scatter[4] = {(const void*)k_scatter_spans<false, false>,
+                            (const void*)k_scatter_spans<false, true>,
+                            (const void*)k_scatter_spans<true, false>,
+                            (const void*)k_scatter_spans<true, true>};
+  for (const void* f : scatter) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace dsmc

@@ -112,6 +112,22 @@ def test_vhs_kn01_multigroup_deterministic(warps, rows):
     assert_bitexact(o, g)
 
 
+@pytest.mark.parametrize("span_particles", [1024, 8192])
+def test_both_scatter_rankings_bitexact(span_particles):
+    """The scatter ranks same-cell records with a shared-memory mask table when at least
+    four of its warps (spans) share an SM, else with __match_any_sync.  1,000 cells of
+    1,200 particles at Kn = 0.1 (particles cross ~13 cells a step): 1,024 particles per
+    span gives 1,000 spans (the mask table on a 152-SM GPU), 8,192 gives 143 spans
+    (match_any); both bit-exact against the oracle over 6 steps."""
+    w = W.VHS_KN01_50M
+    o, g = make_pair(omega=w.omega, Kn=w.Kn, n_cells=1000, ppc=1200, F=w.body_force, seed=5,
+                     span_particles=span_particles)
+    assert g.info()["n_spans"] == (1000 if span_particles == 1024 else 143)
+    o.step(6)
+    g.step(6)
+    assert_bitexact(o, g)
+
+
 @pytest.mark.parametrize("case", [
     dict(n_cells=1, ppc=2, Kn=1.0),                       # one cell, smallest pair
     dict(n_cells=37, ppc=13, Kn=0.5, F=0.01),             # N = 481, ragged warp tail
