@@ -188,9 +188,12 @@ __device__ __forceinline__ const InstParams& stage_instance(const InstParams& on
 }
 
 // Collision models (a.mode): 0 hard spheres, 1 VHS with 0.5 < omega < 1, 2 omega = 1
-// (sigma g independent of g).
+// (sigma g independent of g).  CTAs per SM the register budget is set for: 3 of 8 warps,
+// 6 of 4 warps; the batched 4-warp kernel reads its parameters from shared memory and
+// spills at 6 (85 registers), so it is given 5 (no spills, 10 % faster on the
+// 256-instance batch).
 template <bool kBatch, int kWarps>
-__global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : 6)
+__global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ? 5 : 6))
     k_collide_move(float4* __restrict__ P, const int* __restrict__ off_all,
                    const float* __restrict__ smax_in_all, float* __restrict__ smax_out_all,
                    unsigned long long* __restrict__ ncand_all,
