@@ -112,17 +112,25 @@ def test_vhs_kn01_multigroup_deterministic(warps, rows):
     assert_bitexact(o, g)
 
 
-@pytest.mark.parametrize("span_particles", [1024, 8192])
-def test_both_scatter_rankings_bitexact(span_particles):
+@pytest.mark.parametrize("case", [
+    # particles crossing ~13 cells a step, 1,000 spans: the mask table
+    dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=1024, spans=1000),
+    # the same run in 143 spans: __match_any_sync
+    dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=8192, spans=143),
+    # Kn = 1 on 2,000 cells, particles crossing hundreds of cells a step, 1,000 spans:
+    # the mask table with slices whose cells span 256 values or more (its fallback)
+    dict(Kn=1.0, omega=0.5, n_cells=2000, ppc=600, span_particles=1024, spans=1000),
+])
+def test_both_scatter_rankings_bitexact(case):
     """The scatter ranks same-cell records with a shared-memory mask table when at least
-    four of its warps (spans) share an SM, else with __match_any_sync.  1,000 cells of
-    1,200 particles at Kn = 0.1 (particles cross ~13 cells a step): 1,024 particles per
-    span gives 1,000 spans (the mask table on a 152-SM GPU), 8,192 gives 143 spans
-    (match_any); both bit-exact against the oracle over 6 steps."""
-    w = W.VHS_KN01_50M
-    o, g = make_pair(omega=w.omega, Kn=w.Kn, n_cells=1000, ppc=1200, F=w.body_force, seed=5,
-                     span_particles=span_particles)
-    assert g.info()["n_spans"] == (1000 if span_particles == 1024 else 143)
+    four of its warps (spans) share an SM (a 152-SM GPU: 608 spans), else with
+    __match_any_sync; a slice whose cells span 256 values or more falls back to
+    __match_any_sync inside the mask-table kernel.  Each case bit-exact against the
+    oracle over 6 steps."""
+    c = dict(case)
+    spans = c.pop("spans")
+    o, g = make_pair(F=W.f0_force(c["Kn"]), seed=5, **c)
+    assert g.info()["n_spans"] == spans
     o.step(6)
     g.step(6)
     assert_bitexact(o, g)
