@@ -329,13 +329,9 @@ def run_serve(args, world, rank, local):
     side = torch.cuda.Stream()
     clocks = Clocks(local)
     with torch.cuda.stream(side):
-        # 4-warp CTAs: what dsmc_autotune picks for the batch these requests are drawn
-        # from (a pool's membership changes too often to tune it live; 8 % more
-        # micro-solves/s than 8-warp CTAs on 600 requests)
         pool = DsmcPool(max_particles=args.pool_particles, max_cells=args.pool_particles // 50,
                         max_instances=4096, max_cells_per_instance=1000,
-                        sample_start=args.warmup_steps, graph=True, stream=side.cuda_stream,
-                        cta_warps=4)
+                        sample_start=args.warmup_steps, graph=True, stream=side.cuda_stream)
         barrier(world)
         clocks.start()
         t0 = time.perf_counter()

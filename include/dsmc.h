@@ -95,8 +95,8 @@ typedef struct dsmc_options {
                              Only the work split changes: results are identical for
                              every value; default 0 */
   int cta_warps;          /* warps per CTA of the collide/move pass: 0 keeps the shape
-                             in use (8 at creation, or what dsmc_autotune chose), else 4
-                             or 8; results are identical; default 0 */
+                             in use (8 at creation, 4 for a pool, or what dsmc_autotune
+                             chose), else 4 or 8; results are identical; default 0 */
   int span_rows;          /* sort-matrix rows per span, one per equal part of its
                              slots, each scattered by its own warp: 0 keeps the value
                              in use (1 at creation, or what dsmc_autotune chose), else
