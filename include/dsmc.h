@@ -404,7 +404,9 @@ typedef struct dsmc_surrogate_fit {
   double m_c[4][3];         /* posterior means a_1..a_k of C_k */
   double S_c[4][9];         /* posterior covariances (k x k block of a row-major 3x3) */
   int iterations_c[4];
-  int sel_v, sel_c;         /* selected models: 0 no-slip / 1 slip; k of C_k */
+  int sel_v, sel_c;         /* selected models: 0 no-slip / 1 slip; k of C_k (the
+                               lowest index among log evidences within 1e-9 relative
+                               of the best) */
   double b[3];              /* exponents used */
 } dsmc_surrogate_fit;
 

@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
             L.or_move_particle_open.restype = c.c_int
             L.or_set_open_top.argtypes = [c.c_void_p, c.c_double, c.c_double]
             L.or_set_open_top.restype = None
+            L.or_sincos_turn.argtypes = [c.c_float, fp, fp]
+            L.or_sincos_turn.restype = None
             L.or_scatter_pair.argtypes = [fp, fp, c.c_uint64, c.c_uint32, c.c_uint32,
                                           c.c_uint32, c.c_uint32]
             L.or_scatter_pair.restype = c.c_int
@@ -208,6 +210,14 @@ def move_particle_open(y, vx, vy, vz, dt, F, seed, step, slot, u_top, p_top):
                                       int(seed), int(step) & 0xffffffff, int(slot),
                                       float(u_top), float(p_top))
     return tuple(v.value for v in a), int(err)
+
+
+def sincos_turn(v):
+    """(sin 2 pi v, cos 2 pi v) in binary32 by the oracle's own polynomial."""
+    sn = ctypes.c_float()
+    cs = ctypes.c_float()
+    lib().or_sincos_turn(float(v), ctypes.byref(sn), ctypes.byref(cs))
+    return np.float32(sn.value), np.float32(cs.value)
 
 
 def scatter_pair(vi, vj, seed, k, cell, step, group):

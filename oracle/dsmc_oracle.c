@@ -105,7 +105,7 @@ OR_EXPORT void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
 /* Error bits (same meaning as the library's device error word). */
 #define OR_ERR_NORMAL_ATTEMPTS 1
 #define OR_ERR_BOUNCES 2
-#define OR_ERR_SPHERE_ATTEMPTS 4
+#define OR_ERR_SPHERE_ATTEMPTS 4 /* kept for the bit layout; the direction draw cannot fail */
 #define OR_ERR_CANDIDATES 8
 #define OR_ERR_INFLOW_ATTEMPTS 64
 #define MAX_INFLOW_ATTEMPTS 30 /* sub-draws 16..45 */
@@ -503,35 +503,62 @@ static float accept_threshold(const osim* s, float u, float smax) {
   return or_exp(s->vinv * t);
 }
 
+/* sin(2 pi v) and cos(2 pi v) for v in [0, 1], binary32.  4 v = n + r with n the
+ * nearest integer (4 v, n and r are exact), theta = r pi/2 in [-pi/4, pi/4], the Taylor
+ * series of sin theta through theta^9 and of cos theta through theta^10 (truncation
+ * below 2e-9 on that range) by Horner's rule, then n quarter turns:
+ * (cos, sin)(theta + n pi/2) = (c, s), (-s, c), (-c, -s), (s, -c) for n mod 4 = 0..3. */
+OR_EXPORT void or_sincos_turn(float v, float* sn, float* cs) {
+  float t = 4.0f * v;
+  float n = floorf(t + 0.5f);
+  float r = t - n;
+  float th = r * 0x1.921fb6p+0f; /* pi/2 */
+  float t2 = th * th;
+  float ps = 0x1.71de3ap-19f;    /* 1/9! */
+  ps = ps * t2 - 0x1.a01a02p-13f; /* 1/7! */
+  ps = ps * t2 + 0x1.111112p-7f;  /* 1/5! */
+  ps = ps * t2 - 0x1.555556p-3f;  /* 1/3! */
+  ps = ps * t2;
+  float s = th + th * ps;
+  float pc = -0x1.27e4fcp-22f;   /* -1/10! */
+  pc = pc * t2 + 0x1.a01a02p-16f; /* 1/8! */
+  pc = pc * t2 - 0x1.6c16c2p-10f; /* 1/6! */
+  pc = pc * t2 + 0x1.555556p-5f;  /* 1/4! */
+  pc = pc * t2 - 0.5f;
+  float c = 1.0f + t2 * pc;
+  switch (((int)n) & 3) {
+    case 0: *sn = s; *cs = c; break;
+    case 1: *sn = c; *cs = -s; break;
+    case 2: *sn = -s; *cs = -c; break;
+    default: *sn = -c; *cs = s; break;
+  }
+}
+
 /* Post-collision velocities of an accepted pair (isotropic scattering, which both
  * HS and VHS share): the relative speed g is kept, its direction is drawn uniformly
- * on the sphere by Marsaglia's (1972) method from the sphere sub-draws of the
- * candidate's family, and the centre-of-mass velocity is unchanged.  Returns 0 if
- * the attempts ran out (no change then). */
+ * on the sphere, and the centre-of-mass velocity is unchanged.  The direction comes
+ * from sub-draw 1 of the candidate's family by the cylindrical (Archimedes) map:
+ * n_z = 2 u(w0) - 1 and azimuth 2 pi u(w1) are independent and uniform, so
+ * n = (sqrt(1 - n_z^2) cos, sqrt(1 - n_z^2) sin, n_z) is uniform on the sphere
+ * (the area between two heights is proportional to their distance).  Always succeeds
+ * (returns 1). */
 static int scatter_pair(float* vi, float* vj, float g, const family* f) {
-  for (int a = 0; a < MAX_NORMAL_ATTEMPTS; ++a) {
-    uint32_t w[4];
-    family_draw(f, 1u + (uint32_t)(a >> 1), w);
-    uint32_t w0 = (a & 1) ? w[2] : w[0];
-    uint32_t w1 = (a & 1) ? w[3] : w[1];
-    float a0 = 2.0f * or_u01(w0) - 1.0f;
-    float a1 = 2.0f * or_u01(w1) - 1.0f;
-    float sq = a0 * a0 + a1 * a1;
-    if (sq >= 1.0f) continue;
-    float q = 2.0f * sqrtf(1.0f - sq);
-    float nx = a0 * q;
-    float ny = a1 * q;
-    float nz = 1.0f - 2.0f * sq;
-    float hg = 0.5f * g;
-    float cx = (vi[0] + vj[0]) * 0.5f;
-    float cy = (vi[1] + vj[1]) * 0.5f;
-    float cz = (vi[2] + vj[2]) * 0.5f;
-    float dx = hg * nx, dy = hg * ny, dz = hg * nz;
-    vi[0] = cx + dx; vi[1] = cy + dy; vi[2] = cz + dz;
-    vj[0] = cx - dx; vj[1] = cy - dy; vj[2] = cz - dz;
-    return 1;
-  }
-  return 0;
+  uint32_t w[4];
+  family_draw(f, 1u, w);
+  float nz = 2.0f * or_u01(w[0]) - 1.0f;
+  float rho = sqrtf(1.0f - nz * nz);
+  float sn, cs;
+  or_sincos_turn(or_u01(w[1]), &sn, &cs);
+  float nx = rho * cs;
+  float ny = rho * sn;
+  float hg = 0.5f * g;
+  float cx = (vi[0] + vj[0]) * 0.5f;
+  float cy = (vi[1] + vj[1]) * 0.5f;
+  float cz = (vi[2] + vj[2]) * 0.5f;
+  float dx = hg * nx, dy = hg * ny, dz = hg * nz;
+  vi[0] = cx + dx; vi[1] = cy + dy; vi[2] = cz + dz;
+  vj[0] = cx - dx; vj[1] = cy - dy; vj[2] = cz - dz;
+  return 1;
 }
 
 /* Exposed for the conservation pins: collide vi with vj as an accepted candidate of

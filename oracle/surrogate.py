@@ -170,6 +170,19 @@ def probabilities(log_evidences):
     return w / w.sum()
 
 
+# Two models whose log evidences agree to this relative tolerance are tied (rounding
+# noise, e.g. every extra weight shrunk to zero on data with no signal for it); Eq. 17
+# then ranks them equally and the simpler model, the lower index, is selected.
+TIE_REL = 1e-9
+
+
+def select(log_evidences) -> int:
+    """Eq. 17's most probable model (equal priors), the simplest among ties."""
+    le = np.asarray(log_evidences, np.float64)
+    top = le.max()
+    return int(np.flatnonzero(le >= top - TIE_REL * max(1.0, abs(top)))[0])
+
+
 def train(samples, Kn: float):
     """Fits every boundary and constitutive model to the stacked samples and selects the
     most probable of each kind (Sec. 2.3)."""
@@ -186,8 +199,9 @@ def train(samples, Kn: float):
         c.append(brr(phi[:, :k], t_c))
     pv = probabilities([f["log_evidence"] for f in v])
     pc = probabilities([f["log_evidence"] for f in c])
-    return {"v": v, "c": c, "p_v": pv, "p_c": pc, "sel_v": int(np.argmax(pv)),
-            "sel_c": int(np.argmax(pc))}
+    return {"v": v, "c": c, "p_v": pv, "p_c": pc,
+            "sel_v": select([f["log_evidence"] for f in v]),
+            "sel_c": select([f["log_evidence"] for f in c])}
 
 
 def stress_correction(y, a, b):

@@ -25,7 +25,7 @@ constexpr size_t kSortSmemMax = 200 * 1024;
 // Device error word bits.
 constexpr int kErrNormals = 1;  // Gaussian attempts ran out
 constexpr int kErrBounces = 2;  // wall bounce limit
-constexpr int kErrSphere = 4;   // post-collision direction attempts ran out
+constexpr int kErrSphere = 4;   // reserved (the post-collision direction draw cannot fail)
 constexpr int kErrCandidates = 8;  // a group's candidate count exceeded kMaxCandidates
 constexpr int kErrSort = 16;       // a scatter destination fell outside [0, N)
 constexpr int kErrCopyTimeout = 32;  // a bulk copy into shared memory did not complete

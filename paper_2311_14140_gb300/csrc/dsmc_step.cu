@@ -39,22 +39,48 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Scattering direction from the first of two polar attempts (Marsaglia 1972) that
-// falls inside the unit disc: (a0, a1) gives n = (2 a0 sqrt(1-s), 2 a1 sqrt(1-s),
-// 1 - 2 s), uniform on the sphere.  Returns false when both fall outside.
-__device__ __forceinline__ bool sphere2(const U4& w, float& nx, float& ny, float& nz) {
-  const float a0 = s11(w.x), a1 = s11(w.y);
-  const float b0 = s11(w.z), b1 = s11(w.w);
-  const float sa = fadd(fmul(a0, a0), fmul(a1, a1));
-  const float sb = fadd(fmul(b0, b0), fmul(b1, b1));
-  const bool first = sa < 1.0f;
-  if (!first && !(sb < 1.0f)) return false;
-  const float c0 = first ? a0 : b0, c1 = first ? a1 : b1, sq = first ? sa : sb;
-  const float q = fmul(2.0f, fsqrt(fsub(1.0f, sq)));
-  nx = fmul(c0, q);
-  ny = fmul(c1, q);
-  nz = fsub(1.0f, fmul(2.0f, sq));
-  return true;
+// sin(2 pi v) and cos(2 pi v) for v in [0, 1], binary32: 4 v = n + r with n the nearest
+// integer (4 v, n and r exact), theta = r pi/2 in [-pi/4, pi/4], the Taylor series of
+// sin theta through theta^9 and of cos theta through theta^10 (truncation below 2e-9 on
+// that range) by Horner's rule, then n quarter turns.
+__device__ __forceinline__ void sincos_turn(float v, float& sn, float& cs) {
+  const float t = fmul(4.0f, v);
+  const float n = floorf(fadd(t, 0.5f));
+  const float r = fsub(t, n);
+  const float th = fmul(r, 0x1.921fb6p+0f);  // pi/2
+  const float t2 = fmul(th, th);
+  float ps = 0x1.71de3ap-19f;                  // 1/9!
+  ps = fsub(fmul(ps, t2), 0x1.a01a02p-13f);    // 1/7!
+  ps = fadd(fmul(ps, t2), 0x1.111112p-7f);     // 1/5!
+  ps = fsub(fmul(ps, t2), 0x1.555556p-3f);     // 1/3!
+  ps = fmul(ps, t2);
+  const float s = fadd(th, fmul(th, ps));
+  float pc = -0x1.27e4fcp-22f;                 // -1/10!
+  pc = fadd(fmul(pc, t2), 0x1.a01a02p-16f);    // 1/8!
+  pc = fsub(fmul(pc, t2), 0x1.6c16c2p-10f);    // 1/6!
+  pc = fadd(fmul(pc, t2), 0x1.555556p-5f);     // 1/4!
+  pc = fsub(fmul(pc, t2), 0.5f);
+  const float c = fadd(1.0f, fmul(t2, pc));
+  switch (((int)n) & 3) {
+    case 0: sn = s; cs = c; break;
+    case 1: sn = c; cs = -s; break;
+    case 2: sn = -s; cs = -c; break;
+    default: sn = -c; cs = s; break;
+  }
+}
+
+// Isotropic scattering direction from two uniform words by the cylindrical (Archimedes)
+// map: n_z = 2 u(w0) - 1 and azimuth 2 pi u(w1), independent and uniform, give
+// n = (sqrt(1 - n_z^2) cos, sqrt(1 - n_z^2) sin, n_z), uniform on the sphere.  No
+// rejection, so every candidate of a warp takes the same two draws.
+__device__ __forceinline__ void direction_of(uint32_t w0, uint32_t w1, float& nx, float& ny,
+                                             float& nz) {
+  nz = s11(w0);
+  const float rho = fsqrt(fsub(1.0f, fmul(nz, nz)));
+  float sn, cs;
+  sincos_turn(u01(w1), sn, cs);
+  nx = fmul(rho, cs);
+  ny = fmul(rho, sn);
 }
 
 // The 13 raw moments of one particle (products in binary32, formed as the oracle forms
@@ -294,7 +320,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
   __syncthreads();
   const int n_groups = gfirst[c1 - c0];
 
-  bool bad_bounce = false, sphere_fail = false, cand_fail = false, timeout = false;
+  bool bad_bounce = false, cand_fail = false, timeout = false;
   bool inflow_fail = false;
   uint32_t parity = 0;
   int cur = -1;  // local cell the warp is gathering results for
@@ -385,7 +411,6 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
         bool pend = k < M;
         int i = 0, j = 0;
         float thr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
-        bool have_dir = false;
         if (pend) {
           const U4 w = philox_rk(k, (uint32_t)c, step, c3, a.keys);
           i = (int)__umulhi(w.x, (uint32_t)gn);
@@ -399,15 +424,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
           else
             thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
           const U4 d = philox_rk(k, (uint32_t)c, step, c3 | 1u, a.keys);
-          have_dir = sphere2(d, nx, ny, nz);
-        }
-        if (__any_sync(kFull, pend && !have_dir)) {
-          // Both attempts of the first draw fell outside the disc (4.6 % of candidates).
-          for (int at = 2; at < kNormalAttempts && pend && !have_dir; at += 2) {
-            const U4 d = philox_rk(k, (uint32_t)c, step, c3 | (1u + (uint32_t)(at >> 1)),
-                                   a.keys);
-            have_dir = sphere2(d, nx, ny, nz);
-          }
+          direction_of(d.x, d.y, nx, ny, nz);
         }
         // Earlier candidates of the batch that share a particle with this one: the
         // candidate may be applied once none of them is pending any more, which gives
@@ -433,18 +450,14 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
             const float g = fsqrt(fadd(fadd(fmul(gx, gx), fmul(gy, gy)), fmul(gz, gz)));
             gmax = fmaxf(gmax, g);
             if (g > thr) {
-              if (have_dir) {
-                const float hg = fmul(0.5f, g);
-                const float cx = fmul(fadd(ri.y, rj.y), 0.5f);
-                const float cy = fmul(fadd(ri.z, rj.z), 0.5f);
-                const float cz = fmul(fadd(ri.w, rj.w), 0.5f);
-                const float dx = fmul(hg, nx), dy = fmul(hg, ny), dz = fmul(hg, nz);
-                rec[i] = make_float4(ri.x, fadd(cx, dx), fadd(cy, dy), fadd(cz, dz));
-                rec[j] = make_float4(rj.x, fsub(cx, dx), fsub(cy, dy), fsub(cz, dz));
-                laccn += 1;
-              } else {
-                sphere_fail = true;
-              }
+              const float hg = fmul(0.5f, g);
+              const float cx = fmul(fadd(ri.y, rj.y), 0.5f);
+              const float cy = fmul(fadd(ri.z, rj.z), 0.5f);
+              const float cz = fmul(fadd(ri.w, rj.w), 0.5f);
+              const float dx = fmul(hg, nx), dy = fmul(hg, ny), dz = fmul(hg, nz);
+              rec[i] = make_float4(ri.x, fadd(cx, dx), fadd(cy, dy), fadd(cz, dz));
+              rec[j] = make_float4(rj.x, fsub(cx, dx), fsub(cy, dy), fsub(cz, dz));
+              laccn += 1;
             }
             pend = false;
           }
@@ -501,7 +514,6 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
     flush_cell(gmax, lcand, laccn, ks, kc, sample, &cgmax[cur], &ccand[cur],
                &caccn[cur], cacc + (size_t)cur * kNMom, lane);
   if (bad_bounce) atomicOr(err, kErrBounces);
-  if (sphere_fail) atomicOr(err, kErrSphere);
   if (cand_fail && lane == 0) atomicOr(err, kErrCandidates);
   if (timeout && lane == 0) atomicOr(err, kErrCopyTimeout);
   if (inflow_fail) atomicOr(err, kErrInflow);

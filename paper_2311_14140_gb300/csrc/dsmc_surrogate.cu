@@ -21,6 +21,7 @@
 // on 1x1 to 3x3 matrices, Bishop Sec. 3.5, Tipping App. A) and Eq. 17.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -389,6 +390,20 @@ double zero_evidence(double tt, double N, double* beta) {
   return 0.5 * N * std::log(*beta) - 0.5 * N * std::log(2.0 * M_PI) - 0.5 * (*beta) * tt;
 }
 
+// Eq. 17's most probable model (equal priors), the simplest (lowest index) among models
+// whose log evidences agree with the best to kTieRel: such ties are rounding noise, e.g.
+// every extra weight shrunk to zero on data with no signal for it.
+constexpr double kTieRel = 1e-9;
+
+int select_model(const double* le, int n) {
+  double top = le[0];
+  for (int k = 1; k < n; ++k) top = std::max(top, le[k]);
+  const double tol = kTieRel * std::max(1.0, std::fabs(top));
+  for (int k = 0; k < n; ++k)
+    if (le[k] >= top - tol) return k;
+  return 0;
+}
+
 void probabilities(const double* le, int n, double* p) {
   double mx = le[0];
   for (int i = 1; i < n; ++i) mx = le[i] > mx ? le[i] : mx;
@@ -578,10 +593,8 @@ dsmc_status dsmc_surrogate_train(dsmc_surrogate_handle s, dsmc_surrogate_fit* ou
   }
   probabilities(f.log_evidence_v, 2, f.prob_v);
   probabilities(f.log_evidence_c, 4, f.prob_c);
-  f.sel_v = f.prob_v[1] > f.prob_v[0] ? 1 : 0;
-  f.sel_c = 0;
-  for (int k = 1; k < 4; ++k)
-    if (f.prob_c[k] > f.prob_c[f.sel_c]) f.sel_c = k;
+  f.sel_v = select_model(f.log_evidence_v, 2);
+  f.sel_c = select_model(f.log_evidence_c, 4);
   for (int l = 0; l < 3; ++l) f.b[l] = s->b[l];
   s->fit = f;
   s->fitted = true;

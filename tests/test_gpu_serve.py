@@ -29,6 +29,15 @@ C = dict(Kn=5.0, n_cells=37, ppc=13, omega=0.74, body_force=0.01, seed=17)
 D_ = dict(Kn=0.05, n_cells=211, ppc=55, omega=0.5, body_force=2e-3, seed=2 ** 40 + 7)
 
 
+def vx_tol(m):
+    """Tolerance of a sum of sampled vx between two runs whose states agree bit for bit:
+    the moment sums are binary32 group sums, compensated per warp, and which warp takes
+    which collision group (hence the grouping of the additions) depends on scheduling
+    and CTA shape, so sums agree to the DSMC parity bound 2e-6 * sum |vx|, with
+    sum |vx| <= sqrt(count * sum vx^2) (Cauchy-Schwarz)."""
+    return 2e-6 * np.sqrt(m[:, 0].sum() * m[:, 4].sum())
+
+
 def alone(d, steps, **kw):
     from paper_2311_14140_gb300 import Dsmc
     g = Dsmc(**d, **kw)
@@ -118,7 +127,7 @@ def test_serve_results_equal_the_same_runs_alone(graph):
         g = alone(d, r["steps"], sample_start=8)
         m, n = g.moments()
         assert r["count"] == m[:, 0].sum()
-        np.testing.assert_allclose(r["sum_vx"], m[:, 1].sum(), rtol=1e-9, atol=1e-9)
+        assert abs(r["sum_vx"] - m[:, 1].sum()) <= vx_tol(m)
         if r["converged"] == 1:
             assert r["u_se"] <= 0.3 * abs(r["u_mean"])
     # A, B and C fill the pool (48,576 of 60,000 slots): D waits for one of them
@@ -133,4 +142,6 @@ def test_solve_alone_matches_serving_one_request():
                  max_cells_per_instance=400, sample_start=8)
     r = p.serve([req], epoch_steps=16, batches=4)[0]
     assert s["steps"] == r["steps"] and s["count"] == r["count"]
-    np.testing.assert_allclose(s["sum_vx"], r["sum_vx"], rtol=1e-9, atol=1e-9)
+    # as vx_tol, with sum |vx| below the count (thermal speeds ~N(0, 1/2) in v0 units and
+    # a drift far below 1 give sum |vx| ~ 0.4 count)
+    assert abs(s["sum_vx"] - r["sum_vx"]) <= 2e-6 * s["count"]

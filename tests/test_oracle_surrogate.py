@@ -189,3 +189,14 @@ def test_training_then_bands():
     np.testing.assert_allclose(mean, S.selected_profile(fit, Kn, F, 200, b), rtol=1e-10)
     # the wall value moves by one posterior standard deviation of sigma_P times F
     assert sd[0] == pytest.approx(math.sqrt(2) * math.sqrt(fv["S"][0, 0]) * F, rel=0.05)
+
+
+def test_selection_takes_the_simplest_of_tied_models():
+    """Eq. 17 picks the most probable model; models whose log evidences agree to rounding
+    (1e-9 relative) are tied and the simplest (lowest index) is taken, whichever of them
+    rounding made largest."""
+    assert S.select([-674.977100523768, -674.977100523768, -674.9771005237678,
+                     -674.977100523768]) == 0
+    assert S.select([-5.0, -4.0, -4.0 + 1e-12, -7.0]) == 1
+    assert S.select([-5.0, -4.0, -3.999, -7.0]) == 2
+    assert S.select([10.0, 9.0]) == 0 and S.select([9.0, 10.0]) == 1
