@@ -80,6 +80,9 @@ def lib() -> ctypes.CDLL:
             L.or_move_particle_open.restype = c.c_int
             L.or_set_open_top.argtypes = [c.c_void_p, c.c_double, c.c_double]
             L.or_set_open_top.restype = None
+            L.or_pair_choice.argtypes = [c.c_uint32, c.c_int, c.POINTER(c.c_uint32),
+                                         c.POINTER(c.c_uint32)]
+            L.or_pair_choice.restype = None
             L.or_sincos_turn.argtypes = [c.c_float, fp, fp]
             L.or_sincos_turn.restype = None
             L.or_scatter_pair.argtypes = [fp, fp, c.c_uint64, c.c_uint32, c.c_uint32,
@@ -210,6 +213,14 @@ def move_particle_open(y, vx, vy, vz, dt, F, seed, step, slot, u_top, p_top):
                                       int(seed), int(step) & 0xffffffff, int(slot),
                                       float(u_top), float(p_top))
     return tuple(v.value for v in a), int(err)
+
+
+def pair_choice(w0, ng):
+    """The candidate pair (i, j), i != j, from one 32-bit word."""
+    i = ctypes.c_uint32()
+    j = ctypes.c_uint32()
+    lib().or_pair_choice(int(w0) & 0xFFFFFFFF, int(ng), ctypes.byref(i), ctypes.byref(j))
+    return i.value, j.value
 
 
 def sincos_turn(v):

@@ -480,6 +480,20 @@ OR_EXPORT int or_move_particle_open(float* py, float* pvx, float* pvy, float* pv
   return err;
 }
 
+/* The pair i != j of a candidate among a group's ng particles, from one word by
+ * multiply-shift: i = floor(w0 ng / 2^32); the low half of that product, spread evenly
+ * over [0, 2^32) within each i, gives j = floor(lo (ng - 1) / 2^32), moved past i.
+ * Each ordered pair receives floor or ceil of 2^32 / (ng (ng - 1)) words, so within
+ * ng^2 / 2^32 (3.4e-5 at ng = 383) of uniform. */
+OR_EXPORT void or_pair_choice(uint32_t w0, int ng, uint32_t* i, uint32_t* j) {
+  uint64_t p = (uint64_t)w0 * (uint64_t)ng;
+  uint32_t a = (uint32_t)(p >> 32);
+  uint32_t b = (uint32_t)(((uint64_t)(uint32_t)p * (uint64_t)(ng - 1)) >> 32);
+  if (b >= a) b += 1;
+  *i = a;
+  *j = b;
+}
+
 /* sigma(g) g in units of sigma_ref v0: g for hard spheres, cvhs g^(2-2w) for VHS. */
 static float sigma_g(const osim* s, float g) {
   if (s->omega == 0.5) return g;
@@ -537,18 +551,16 @@ OR_EXPORT void or_sincos_turn(float v, float* sn, float* cs) {
 /* Post-collision velocities of an accepted pair (isotropic scattering, which both
  * HS and VHS share): the relative speed g is kept, its direction is drawn uniformly
  * on the sphere, and the centre-of-mass velocity is unchanged.  The direction comes
- * from sub-draw 1 of the candidate's family by the cylindrical (Archimedes) map:
- * n_z = 2 u(w0) - 1 and azimuth 2 pi u(w1) are independent and uniform, so
+ * from the words w2, w3 of the candidate's draw by the cylindrical (Archimedes) map:
+ * n_z = 2 u(w2) - 1 and azimuth 2 pi u(w3) are independent and uniform, so
  * n = (sqrt(1 - n_z^2) cos, sqrt(1 - n_z^2) sin, n_z) is uniform on the sphere
  * (the area between two heights is proportional to their distance).  Always succeeds
  * (returns 1). */
-static int scatter_pair(float* vi, float* vj, float g, const family* f) {
-  uint32_t w[4];
-  family_draw(f, 1u, w);
-  float nz = 2.0f * or_u01(w[0]) - 1.0f;
+static int scatter_pair(float* vi, float* vj, float g, uint32_t w2, uint32_t w3) {
+  float nz = 2.0f * or_u01(w2) - 1.0f;
   float rho = sqrtf(1.0f - nz * nz);
   float sn, cs;
-  or_sincos_turn(or_u01(w[1]), &sn, &cs);
+  or_sincos_turn(or_u01(w3), &sn, &cs);
   float nx = rho * cs;
   float ny = rho * sn;
   float hg = 0.5f * g;
@@ -567,8 +579,9 @@ OR_EXPORT int or_scatter_pair(float* vi, float* vj, uint64_t seed, uint32_t k,
                               uint32_t cell, uint32_t step, uint32_t group) {
   float gx = vi[0] - vj[0], gy = vi[1] - vj[1], gz = vi[2] - vj[2];
   float g = sqrtf(gx * gx + gy * gy + gz * gz);
-  family f = {seed, k, cell, step, (TAG_COLL << 24) | (group << 4), 0};
-  return scatter_pair(vi, vj, g, &f);
+  uint32_t w[4];
+  draw(seed, k, cell, step, (TAG_COLL << 24) | (group << 4), w);
+  return scatter_pair(vi, vj, g, w[2], w[3]);
 }
 
 /* Exposed for the acceptance pin. */
@@ -617,19 +630,17 @@ static void collide_group(osim* s, int c, int nc, int gic, int start, int ng) {
   float* vz = s->vz + start;
   for (uint32_t k = 0; k < M; ++k) {
     draw(s->seed, k, (uint32_t)c, st, c3, w);
-    uint32_t i = (uint32_t)(((uint64_t)w[0] * (uint64_t)ng) >> 32);
-    uint32_t j = (uint32_t)(((uint64_t)w[1] * (uint64_t)(ng - 1)) >> 32);
-    if (j >= i) j += 1;
+    uint32_t i, j;
+    or_pair_choice(w[0], ng, &i, &j);
     float gx = vx[i] - vx[j];
     float gy = vy[i] - vy[j];
     float gz = vz[i] - vz[j];
     float g = sqrtf(gx * gx + gy * gy + gz * gz);
     if (g > s->gmax_obs[c]) s->gmax_obs[c] = g;
-    if (g > accept_threshold(s, or_u01(w[2]), smax)) {
+    if (g > accept_threshold(s, or_u01(w[1]), smax)) {
       float vi[3] = {vx[i], vy[i], vz[i]};
       float vj[3] = {vx[j], vy[j], vz[j]};
-      family f = {s->seed, k, (uint32_t)c, st, c3, 0};
-      if (!scatter_pair(vi, vj, g, &f)) {
+      if (!scatter_pair(vi, vj, g, w[2], w[3])) {
         s->err |= OR_ERR_SPHERE_ATTEMPTS;
         continue;
       }

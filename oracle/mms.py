@@ -48,16 +48,26 @@ def interface_velocity(u_cfd, L_d: float) -> float:
 
 def mms_hybrid(Kn: float, F: float, *, omega: float = 0.5, dy: float = 0.005, ppc: int = 50,
                buffer: int = 5, iterations: int = 3, steps: int = 400, window: int = 20,
-               warmup: int = 200, n_cfd: int = 200, seed: int = 0, G: int = 256):
+               warmup: int = 200, n_cfd: int = 200, seed: int = 0, G: int = 256,
+               interface=None):
+    """The MMS hybrid (Sec. 2, Sec. 3.2).  `interface`, if given, is a list of (u, P)
+    pairs used at the DSMC's open boundary in each iteration instead of the values from
+    the current CFD profile (a test drives the oracle with the library's interface
+    history this way, so that both sides' DSMC layers run bit for bit alike even where
+    rounding of the fitted profiles makes the binary32 interface values differ); the
+    values the oracle's own profiles give are returned as "interface_own"."""
     b = S.exponents(Kn)
     n_train, n_sub, L_d = layer_geometry(Kn, dy, buffer)
     sim = oracle.OracleSim(omega=omega, Kn=Kn / L_d, F=F * L_d, n_cells=n_sub, ppc=ppc,
                            seed=seed, G=G, sample_start=0)
     u_cfd = S.cfd(Kn, F, n_cfd)  # no-slip Navier-Stokes to start
-    samples, history, fit = [], [], None
+    samples, history, own, fit = [], [], [], None
     for it in range(iterations):
         u_if = interface_velocity(u_cfd, L_d)
         p_if = F * (2.0 * L_d - 1.0)
+        own.append((u_if, p_if))
+        if interface is not None:
+            u_if, p_if = interface[it]
         sim.set_open_top(u_if, p_if)
         history.append((float(np.float32(u_if)), float(np.float32(p_if))))
         if it == 0 and warmup:
@@ -72,5 +82,6 @@ def mms_hybrid(Kn: float, F: float, *, omega: float = 0.5, dy: float = 0.005, pp
         u_cfd = S.selected_profile(fit, Kn, F, n_cfd, b)
     err = sim.error
     sim.close()
-    return {"fit": fit, "profile": u_cfd, "interface": history, "n_train": n_train,
+    return {"fit": fit, "profile": u_cfd, "interface": history, "interface_own": own,
+            "n_train": n_train,
             "n_sub": n_sub, "L_d": L_d, "b": b, "samples": len(samples), "error": err}

@@ -412,19 +412,22 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
         int i = 0, j = 0;
         float thr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
         if (pend) {
+          // one draw per candidate: word 0 the pair (multiply-shift: i from the high
+          // half of w0 gn, j from the low half times gn - 1), word 1 the acceptance
+          // uniform, words 2 and 3 the scattering direction
           const U4 w = philox_rk(k, (uint32_t)c, step, c3, a.keys);
-          i = (int)__umulhi(w.x, (uint32_t)gn);
-          j = (int)__umulhi(w.y, (uint32_t)(gn - 1));
+          const unsigned long long pij = (unsigned long long)w.x * (unsigned long long)gn;
+          i = (int)(pij >> 32);
+          j = (int)__umulhi((uint32_t)pij, (uint32_t)(gn - 1));
           j += (j >= i) ? 1 : 0;
-          const float us = fmul(u01(w.z), smax);
+          const float us = fmul(u01(w.y), smax);
           if (mode == 0)
             thr = us;
           else if (mode == 1)
             thr = exp32(fmul(a.vinv, fsub(ln32(us), a.lncv)));
           else
             thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
-          const U4 d = philox_rk(k, (uint32_t)c, step, c3 | 1u, a.keys);
-          direction_of(d.x, d.y, nx, ny, nz);
+          direction_of(w.z, w.w, nx, ny, nz);
         }
         // Earlier candidates of the batch that share a particle with this one: the
         // candidate may be applied once none of them is pending any more, which gives

@@ -132,6 +132,37 @@ def test_collision_conserves_momentum_and_energy():
     assert worst_e < 1e-5
 
 
+def test_pair_choice_is_uniform_over_ordered_pairs():
+    """The candidate pair from one word (multiply-shift): always i != j within the group;
+    for ng = 2..6 the count of words per ordered pair, over an evenly spaced grid of 2^20
+    words covering [0, 2^32), is within 1 of equal (exactly as floor/ceil of the share);
+    and random words give a chi-square consistent with uniform pairs at ng = 7."""
+    rng = np.random.default_rng(12)
+    for ng in (2, 3, 5, 17, 256, 383):
+        for w in rng.integers(0, 2 ** 32, 2000, dtype=np.uint64):
+            i, j = oracle.pair_choice(int(w), ng)
+            assert 0 <= i < ng and 0 <= j < ng and i != j
+    step = 2 ** 12
+    for ng in range(2, 7):
+        counts = {}
+        for w in range(0, 2 ** 32, step):
+            p = oracle.pair_choice(w, ng)
+            counts[p] = counts.get(p, 0) + 1
+        assert len(counts) == ng * (ng - 1)
+        share = (2 ** 32 // step) / (ng * (ng - 1))
+        assert max(abs(v - share) for v in counts.values()) <= 1.0
+    ng, n = 7, 84_000
+    counts = np.zeros((ng, ng))
+    for w in rng.integers(0, 2 ** 32, n, dtype=np.uint64):
+        i, j = oracle.pair_choice(int(w), ng)
+        counts[i, j] += 1
+    obs = counts[~np.eye(ng, dtype=bool)]
+    exp = n / (ng * (ng - 1))
+    chi2 = ((obs - exp) ** 2 / exp).sum()
+    from scipy import stats
+    assert stats.chi2.sf(chi2, ng * (ng - 1) - 1) > 1e-3
+
+
 def test_sincos_turn_exact_quarter_turns():
     """The oracle's binary32 sin/cos of 2 pi v: at whole quarter turns the reduced angle
     is exactly 0 and the values are exact."""
