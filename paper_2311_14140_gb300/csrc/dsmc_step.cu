@@ -11,9 +11,10 @@
 //                      1. load the group's records, keep them in shared memory and add
 //                         their moment sums before the collisions,
 //                      2. draw every NTC candidate's pair, acceptance threshold and
-//                         scattering direction up front (32 candidates at a time, one
-//                         per lane), then apply the candidates in conflict-free rounds
-//                         that reproduce the sequential order exactly,
+//                         scattering direction up front (one Philox draw per candidate,
+//                         32 candidates at a time, one per lane), then apply the
+//                         candidates in conflict-free rounds that reproduce the
+//                         sequential order exactly,
 //                      3. per particle: add the moment sums after the collisions, fly
 //                         with the body force and diffuse walls, store the record back
 //                         in place and count its new cell in the CTA's histogram.
@@ -23,11 +24,12 @@
 //                    counts cells of the span's slots (the sort into cells at creation
 //                    and after a state load).
 //   k_scatter_spans  one warp per span: re-reads the records in slot order, 16 per lane
-//                    in flight, and scatters them stably into the other buffer from the
-//                    span's row of the prefix-summed matrix plus the new cell offsets.
+//                    in flight, ranks each record among the same-cell records before it
+//                    and scatters it stably into the other buffer from the span's row of
+//                    the prefix-summed matrix plus the new cell offsets.
 //
-// Between them, k_scan_hist and k_cell_offsets (dsmc_kernels.cu) turn the matrix into
-// per-span bases and the new cell offsets.
+// Between them, k_scan_spans and k_offsets_cells (below) turn the matrix into per-span
+// bases and the new cell offsets.
 #include <climits>
 
 #include "dsmc_device.cuh"
