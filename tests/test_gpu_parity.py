@@ -117,6 +117,9 @@ def test_vhs_kn01_multigroup_deterministic(warps, rows):
     dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=1024, spans=1000),
     # the same run in 143 spans: __match_any_sync
     dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=8192, spans=143),
+    # 1,000 spans of two sort rows each (a warp per row): the mask table on half-spans
+    dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=1024, span_rows=2,
+         spans=1000),
     # Kn = 1 on 2,000 cells, particles crossing hundreds of cells a step, 1,000 spans:
     # the mask table with slices whose cells span 256 values or more (its fallback)
     dict(Kn=1.0, omega=0.5, n_cells=2000, ppc=600, span_particles=1024, spans=1000),
