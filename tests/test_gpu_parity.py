@@ -149,6 +149,7 @@ def test_both_scatter_rankings_bitexact(case):
     dict(n_cells=8, ppc=1500, Kn=0.3, G=512, omega=0.81),  # largest groups
     dict(n_cells=64, ppc=250, Kn=1.0, collisions=False),  # sampling without collisions
     dict(n_cells=33, ppc=97, Kn=0.7, sample_start=7, dt_factor=0.5),
+    dict(n_cells=16384, ppc=60, Kn=0.5, F=0.002),         # the largest cell count
 ])
 def test_edge_cases_deterministic(case):
     c = dict(case)
