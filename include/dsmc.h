@@ -77,6 +77,18 @@ typedef enum dsmc_status {
   DSMC_E_STATE = 5         /* call not valid in the handle's current state */
 } dsmc_status;
 
+/* Arithmetic of the per-cell moment sums (dsmc_options.accum).  Both forms products of
+ * the binary32 velocities; a group's sums are then combined exactly (fixed point in
+ * the cell's grid, integer addition), so the sums do not depend on which warp takes
+ * which group, and accumulated over steps in binary64.
+ *   DSMC_ACCUM_FP32: each lane adds its particles' products in binary32 (second and
+ *     third moments by fused multiply-add) and the warp sums them in binary32: at most
+ *     28 roundings of relative size 2^-24 on partial sums bounded by the sum of
+ *     |products|.  The default.
+ *   DSMC_ACCUM_FP64: every product is rounded to binary32 (as a plain CPU DSMC forms
+ *     it) and added in binary64 from the first addition on. */
+typedef enum dsmc_accum { DSMC_ACCUM_FP32 = 0, DSMC_ACCUM_FP64 = 1 } dsmc_accum;
+
 /* Options.  Get the defaults from dsmc_default_options and change fields. */
 typedef struct dsmc_options {
   double dt_factor;       /* dt = dt_factor / nu, nu = n sigma_ref <g> the equilibrium
@@ -105,6 +117,8 @@ typedef struct dsmc_options {
                              CUDA graph (captured on first use; needs a stream other
                              than the legacy default; off while profiling); results
                              are identical; default 0 */
+  int accum;              /* dsmc_accum: arithmetic of the moment sums; default
+                             DSMC_ACCUM_FP32 */
   void* stream;           /* cudaStream_t for all work; default NULL */
 } dsmc_options;
 
@@ -196,6 +210,27 @@ DSMC_API dsmc_status dsmc_sync(dsmc_handle h);
  * half before and half after its collisions.  Velocities in v0.  *n_samples gets
  * the number of sampled steps.  Synchronises. */
 DSMC_API dsmc_status dsmc_sample_moments(dsmc_handle h, double* out, long long* n_samples);
+
+/* Number of cell fields returned by dsmc_cell_fields. */
+#define DSMC_NFIELD 9
+
+/* Cell fields from raw moment sums: the time averages the paper reports for its DSMC
+ * (Sec. 3), in the units of Eq. 6.  sums holds n_cells x DSMC_NMOM raw sums (the layout
+ * of dsmc_sample_moments) over n_samples >= 1 sampled steps of a run with ppc >= 1
+ * particles per cell at start; out gets n_cells x DSMC_NFIELD values, row-major per
+ * cell:
+ *   [0] n   = count / (n_samples ppc)        density relative to the initial one
+ *   [1..3] u_i = sum v_i / count              mean velocity (v0)
+ *   [4] T   = (2/3) (<|v|^2> - |u|^2)         temperature (T0)
+ *   [5] Pxy = 2 n (<vx vy> - ux uy)           shear stress (P0 = n0 k T0; rho/P0 = 2/v0^2)
+ *   [6..8] q_i = n <c_i |c|^2>, c = v - u     heat flux (P0 v0)
+ * A cell without samples gives n = 0 and NaN elsewhere.  Host memory; binary64. */
+DSMC_API dsmc_status dsmc_cell_fields(const double* sums, long long n_samples, int ppc,
+                                      int n_cells, double* out);
+
+/* The same fields from instance i's own sums (computed on the device); out (host or
+ * device memory) gets its n_cells x DSMC_NFIELD values.  Synchronises. */
+DSMC_API dsmc_status dsmc_cell_fields_of(dsmc_handle h, int i, double* out);
 
 /* Zero the moment sums and collision counters (enqueued). */
 DSMC_API dsmc_status dsmc_reset_samples(dsmc_handle h);
@@ -559,11 +594,15 @@ DSMC_API dsmc_status dsmc_destroy(dsmc_handle h);
  * memory and lends them no allocator, or latency-sensitive loops that must avoid the
  * device-wide synchronisation of cudaMalloc/cudaFree.
  * Inputs y, vx, vy, vz and outputs y_out, vx_out, vy_out, vz_out (n_particles floats
- * each) and offset_out (n_cells + 1 ints) are caller-owned device memory; outputs
- * must not alias inputs.  On return (asynchronously, on `stream`) the outputs hold
- * the state ordered by cell, cell = trunc(y * n_cells) clamped to [0, n_cells - 1],
- * particles of one cell in their input order, and offset_out[c] is the first slot of
- * cell c (offset_out[n_cells] = n_particles), exactly as dsmc_load_state sorts.
+ * each) and offset_out (n_cells + 1 ints) are caller-owned device memory; an output
+ * that overlaps an input or another output is rejected (DSMC_E_INVAL).  On completion
+ * (asynchronously, on `stream`) the outputs hold the state ordered by cell,
+ * cell = trunc(y * n_cells) clamped to [0, n_cells - 1], particles of one cell in their
+ * input order, and offset_out[c] is the first slot of cell c
+ * (offset_out[n_cells] = n_particles), exactly as dsmc_load_state sorts.  Device-side
+ * failure: if the inputs changed while the sort ran (for instance an overlapping call
+ * on the shared scratch), the kernels write no record outside the outputs and set
+ * offset_out[n_cells] = -1 instead; read it with the outputs after synchronising.
  * Scratch: a fixed 8 MiB array compiled into the library, held by every GPU that
  * loads it until the process exits.  Calls on one GPU that overlap in time (other
  * streams or threads) share it and race.  The first call on each device looks up the

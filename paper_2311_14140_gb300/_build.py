@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libdsmc.so")
 SOURCES = ["dsmc_kernels.cu", "dsmc_step.cu", "dsmc_capi.cu", "dsmc_noalloc.cu",
-           "dsmc_serve.cu", "dsmc_surrogate.cu", "dsmc_mms.cu", "dsmc_gp.cu"]
+           "dsmc_serve.cu", "dsmc_surrogate.cu", "dsmc_mms.cu", "dsmc_gp.cu",
+           "dsmc_fields.cu"]
 HEADERS = ["dsmc_device.cuh", "dsmc_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

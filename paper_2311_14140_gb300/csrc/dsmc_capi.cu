@@ -140,6 +140,8 @@ dsmc_status check_options(const dsmc_options* o) {
     return fail(DSMC_E_INVAL, "options: span_rows must be 0, 1 or 2");
   if (o->graph && o->stream == nullptr)
     return fail(DSMC_E_INVAL, "options: graph replay needs a stream other than the legacy default");
+  if (o->accum != DSMC_ACCUM_FP32 && o->accum != DSMC_ACCUM_FP64)
+    return fail(DSMC_E_INVAL, "options: accum must be DSMC_ACCUM_FP32 or DSMC_ACCUM_FP64");
   return DSMC_OK;
 }
 
@@ -220,7 +222,8 @@ struct Capacity {
 
 // Byte offsets of the arrays in the device workspace.
 struct Layout {
-  size_t st, hist, count, offset, smax, ncand, nacc, acc, tab, span_inst, chan, err, total;
+  size_t st, hist, count, offset, smax, ncand, nacc, acc, fields, tab, span_inst, chan, err,
+      total;
 };
 
 long long padded_slots(long long N) { return (N + 63) & ~63LL; }
@@ -253,6 +256,8 @@ Layout layout_of(const Capacity& C) {
   o += align256((size_t)C.cells * sizeof(unsigned long long));
   L.acc = o;
   o += align256((size_t)C.cells * kNMom * sizeof(double));
+  L.fields = o;
+  o += align256((size_t)C.cells * DSMC_NFIELD * sizeof(double));
   L.tab = o;
   o += align256(2 * (size_t)C.inst * sizeof(InstParams));
   L.span_inst = o;
@@ -355,6 +360,7 @@ struct dsmc_sim {
   int scur = 0;
   unsigned long long *ncand = nullptr, *nacc = nullptr;
   double* acc = nullptr;
+  double* fields = nullptr;  // dsmc_cell_fields_of's output on the device
   InstParams* tab_dev = nullptr;  // [0, C.inst): the step's; [C.inst, 2 C.inst): admission
   int* span_inst_dev = nullptr;   // likewise with C.spans entries each
   double* chan_dev = nullptr;
@@ -547,6 +553,7 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   L.gstep = h->gstep;
   L.gstep_dev = h->capturing ? h->gstep_dev : nullptr;
   L.count_only = count_only ? 1 : 0;
+  L.accum = h->opt.accum;
   return L;
 }
 
@@ -693,6 +700,7 @@ dsmc_status read_error_word(dsmc_sim* h) {
     if (v & kErrSort) what += " sort-destination";
     if (v & kErrCopyTimeout) what += " bulk-copy-timeout";
     if (v & kErrInflow) what += " inflow-attempts";
+    if (v & kErrMoments) what += " moment-range";
     return fail(DSMC_E_DEVICE_LIMIT, "device limit reached:" + what);
   }
   return DSMC_OK;
@@ -894,6 +902,7 @@ dsmc_status new_handle(const Capacity& C, const dsmc_options& opt, bool pool, vo
   h->ncand = (unsigned long long*)(b + L.ncand);
   h->nacc = (unsigned long long*)(b + L.nacc);
   h->acc = (double*)(b + L.acc);
+  h->fields = (double*)(b + L.fields);
   h->tab_dev = (InstParams*)(b + L.tab);
   h->span_inst_dev = (int*)(b + L.span_inst);
   h->chan_dev = (double*)(b + L.chan);
@@ -1005,6 +1014,7 @@ dsmc_status dsmc_default_options(dsmc_options* opt) {
   opt->cta_warps = 0;
   opt->span_rows = 0;
   opt->graph = 0;
+  opt->accum = DSMC_ACCUM_FP32;
   opt->stream = nullptr;
   return DSMC_OK;
 }
@@ -1289,6 +1299,24 @@ dsmc_status dsmc_sample_moments_of(dsmc_handle h, int id, double* out, long long
 
 dsmc_status dsmc_sample_moments(dsmc_handle h, double* out, long long* n_samples) {
   return dsmc_sample_moments_of(h, 0, out, n_samples);
+}
+
+dsmc_status dsmc_cell_fields_of(dsmc_handle h, int id, double* out) {
+  dsmc_status s = check_index(h, id);
+  if (s != DSMC_OK) return s;
+  if (!out) return fail(DSMC_E_INVAL, "out: NULL");
+  DeviceGuard guard(h->device);
+  if ((s = admit_fresh(h)) != DSMC_OK) return s;
+  const Inst& x = h->inst[id];
+  if (x.n_samples < 1) return fail(DSMC_E_STATE, "cell fields: no sampled steps yet");
+  double* f = h->fields + (size_t)x.cell_base * DSMC_NFIELD;
+  DSMC_CUDA(launch_cell_fields(h->acc + (size_t)x.cell_base * kNMom, x.n_cells, x.n_samples,
+                               x.ppc, f, h->stream()),
+            "cell fields");
+  DSMC_CUDA(cudaMemcpyAsync(out, f, (size_t)x.n_cells * DSMC_NFIELD * sizeof(double),
+                            cudaMemcpyDefault, h->stream()),
+            "copy cell fields");
+  return dsmc_sync(h);
 }
 
 dsmc_status dsmc_sample_moments_all(dsmc_handle h, double* out, long long* n_samples) {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dsmc.h"
+
 #include <string>
 
 namespace dsmc {
@@ -30,6 +32,7 @@ constexpr int kErrCandidates = 8;  // a group's candidate count exceeded kMaxCan
 constexpr int kErrSort = 16;       // a scatter destination fell outside [0, N)
 constexpr int kErrCopyTimeout = 32;  // a bulk copy into shared memory did not complete
 constexpr int kErrInflow = 64;       // an open-boundary emission ran out of attempts
+constexpr int kErrMoments = 128;     // a group's moment total exceeded the fixed-point range
 
 // Largest NTC candidate count of one group in one step (about 80 on the largest
 // workload): anything above means corrupted (sigma g)_max and is skipped.
@@ -176,7 +179,10 @@ struct StepLaunch {
   long long* gstep_dev;  // non-NULL (graph replay): read the step number here instead;
                          // the cell-offset kernel advances it at the end of the step
   int count_only;
+  int accum;  // DSMC_ACCUM_FP32 or DSMC_ACCUM_FP64: per-lane moment sums
 };
+cudaError_t launch_cell_fields(const double* acc, int n_cells, long long n_samples, int ppc,
+                               double* out, cudaStream_t st);
 cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
                                 float* smax_out, unsigned long long* ncand,
                                 unsigned long long* nacc, double* acc, int* hist,

@@ -6,17 +6,17 @@
 //                     velocity components N(0, 1/2) (gas at rest at the wall
 //                     temperature, Sec. 2.1, units of Eq. 6)
 //   k_move_count      (optional free flight,) new cell, warp-private histogram over
-//                     fixed spans of slots: the sort into cells at creation, after a
-//                     state load, and in the allocation-free sort
+//                     fixed spans of slots
 //   k_scan_hist       per cell, exclusive prefix of the histogram over partitions
-//                     (also used by every step)
 //   k_cell_offsets    exclusive prefix over cells -> first slot of each cell
 //   k_scatter         stable counting-sort scatter into the other buffer
 // The two state passes of a step are in dsmc_step.cu.
 //
-// The state is structure-of-arrays binary32 (y, vx, vy, vz), double-buffered for
-// the sort.  Kernel launches live in the host file; declarations are in
-// dsmc_internal.h.
+// The resident state of a run is an array of float4 records (y, vx, vy, vz),
+// double-buffered for the sort; k_init writes records.  k_move_count, k_scan_hist,
+// k_cell_offsets and k_scatter serve only the allocation-free sort, whose caller owns
+// four binary32 arrays (y, vx, vy, vz).  Kernel launches live in the host file;
+// declarations are in dsmc_internal.h.
 #include <climits>
 
 #include "dsmc_device.cuh"

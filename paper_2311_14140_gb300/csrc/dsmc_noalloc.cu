@@ -17,8 +17,14 @@
 // stand-in), so the first call on each device looks the address up with
 // cudaGetSymbolAddress while that device is current, and later calls reuse it.  That
 // first call should come before any stream capture on that device.
+//
+// A destination outside [0, n_particles) (which only inputs changing while the sort runs,
+// such as an overlapping call, can produce) is never written: the scatter records it in
+// the scratch's error word, and a last one-thread kernel turns a non-zero error word into
+// offset_out[n_cells] = -1, which the caller reads with the outputs.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -32,9 +38,21 @@ constexpr size_t kStaticScratchInts = kStaticScratchBytes / sizeof(int);
 // totals, then the sort-partition histogram (n_warps x n_cells).
 static __device__ __align__(256) int g_static_scratch[kStaticScratchInts];
 
+// offset_out[n_cells] = -1 when a kernel of this sort recorded an error.
+__global__ void k_flag_sort_error(const int* __restrict__ err, int* __restrict__ offset_out,
+                                  int n_cells) {
+  if (*err != 0) offset_out[n_cells] = -1;
+}
+
 namespace {
 
 constexpr int kMaxDevices = 64;
+
+// Do the byte ranges [a, a + na) and [b, b + nb) share a byte?
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
 
 std::mutex g_setup_mutex;
 int* g_scratch_addr[kMaxDevices] = {};
@@ -72,6 +90,24 @@ extern "C" dsmc_status dsmc_sort_cells_static(const float* y, const float* vx, c
     return reject(DSMC_E_INVAL, "dsmc_sort_cells_static: n_particles must be <= 2^31 - 2^24");
   if ((size_t)n_cells * sizeof(int) > kSortSmemMax)
     return reject(DSMC_E_INVAL, "dsmc_sort_cells_static: n_cells must be <= 51200");
+  // Every output must be disjoint from every input and from the other outputs: the
+  // scatter writes outputs while other warps still read inputs.
+  {
+    const size_t fb = (size_t)n_particles * sizeof(float);
+    const void* in[4] = {y, vx, vy, vz};
+    const void* outp[5] = {y_out, vx_out, vy_out, vz_out, offset_out};
+    const size_t outb[5] = {fb, fb, fb, fb, ((size_t)n_cells + 1) * sizeof(int)};
+    for (int o = 0; o < 5; ++o) {
+      for (int i = 0; i < 4; ++i)
+        if (overlap(outp[o], outb[o], in[i], fb))
+          return reject(DSMC_E_INVAL,
+                        "dsmc_sort_cells_static: an output overlaps an input array");
+      for (int o2 = 0; o2 < o; ++o2)
+        if (overlap(outp[o], outb[o], outp[o2], outb[o2]))
+          return reject(DSMC_E_INVAL,
+                        "dsmc_sort_cells_static: two output arrays overlap");
+    }
+  }
   // Partition of the particles into warp spans: as many spans as the scratch holds
   // histogram rows for, at most the library's usual count.
   const size_t rows_fit = (kStaticScratchInts - 64 - (size_t)n_cells) / (size_t)n_cells;
@@ -91,9 +127,14 @@ extern "C" dsmc_status dsmc_sort_cells_static(const float* y, const float* vx, c
 
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
-  if (e != cudaSuccess || device < 0 || device >= kMaxDevices)
+  if (e != cudaSuccess)
     return reject(DSMC_E_CUDA, std::string("dsmc_sort_cells_static: cudaGetDevice: ") +
                               cudaGetErrorString(e));
+  if (device < 0 || device >= kMaxDevices)
+    return reject(DSMC_E_CUDA, "dsmc_sort_cells_static: device index " +
+                                   std::to_string(device) + " is beyond the " +
+                                   std::to_string(kMaxDevices) + " devices it keeps scratch "
+                                   "addresses for");
   int* scratch = nullptr;
   e = scratch_address(device, &scratch);
   if (e != cudaSuccess)
@@ -118,6 +159,10 @@ extern "C" dsmc_status dsmc_sort_cells_static(const float* y, const float* vx, c
   if (e == cudaSuccess) e = launch_cell_offsets(count, n_cells, offset_out, st);
   if (e == cudaSuccess)
     e = launch_scatter(in, out, n_particles, plan, n_cells, ncf, hist, offset_out, err, st);
+  if (e == cudaSuccess) {
+    k_flag_sort_error<<<1, 1, 0, st>>>(err, offset_out, n_cells);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess)
     return reject(DSMC_E_CUDA, std::string("dsmc_sort_cells_static: ") + cudaGetErrorString(e));
   return DSMC_OK;

@@ -31,6 +31,7 @@
 // Between them, k_scan_spans and k_offsets_cells (below) turn the matrix into per-span
 // bases and the new cell offsets.
 #include <climits>
+#include <type_traits>
 
 #include "dsmc_device.cuh"
 #include "dsmc_internal.h"
@@ -85,102 +86,150 @@ __device__ __forceinline__ void direction_of(uint32_t w0, uint32_t w1, float& nx
   ny = fmul(rho, sn);
 }
 
-// The 13 raw moments of one particle (products in binary32, formed as the oracle forms
-// them), added in pairs with packed binary32 arithmetic.
-struct Moments {
-  float2 a, b, c, d, e;  // (1, vx) (vy, vz) (vx2, vy2) (vz2, vxvy) (vxvz, vyvz)
-  float2 g;              // (vx v2, vy v2)
-  float h;               // vz v2
+// Per-lane sums of the 12 velocity moments of a group's particles (the count is the
+// cell's particle number and needs no sum): v, v_i v_j (six), v_i |v|^2 (three).
+// LaneSums<float>: the products of the binary32 velocities summed in binary32, the
+// second and third moments by fused multiply-add (one rounding per term).
+// LaneSums<double>: every product rounded to binary32 exactly as the oracle forms it,
+// then added in binary64.
+template <typename T>
+struct LaneSums;
+
+template <>
+struct LaneSums<float> {
+  float2 a, b, c, d, e, f;  // (vx, vy) (vz, vz2) (vx2, vy2) (vxvy, vxvz) (vyvz, vz v2) (vx v2, vy v2)
   __device__ __forceinline__ void zero() {
-    a = b = c = d = e = g = make_float2(0.0f, 0.0f);
-    h = 0.0f;
+    a = b = c = d = e = f = make_float2(0.0f, 0.0f);
   }
   __device__ __forceinline__ void add(float x, float y, float z) {
     const float2 xy = make_float2(x, y);
     const float2 sq = __fmul2_rn(xy, xy);
     const float zz = fmul(z, z);
     const float v2 = fadd(fadd(sq.x, sq.y), zz);
-    a = __fadd2_rn(a, make_float2(1.0f, x));
-    b = __fadd2_rn(b, make_float2(y, z));
+    a = __fadd2_rn(a, xy);
+    b = __fadd2_rn(b, make_float2(z, zz));
     c = __fadd2_rn(c, sq);
-    d = __fadd2_rn(d, make_float2(zz, fmul(x, y)));
-    e = __fadd2_rn(e, __fmul2_rn(make_float2(x, y), make_float2(z, z)));
-    g = __fadd2_rn(g, __fmul2_rn(xy, make_float2(v2, v2)));
-    h = fadd(h, fmul(z, v2));
+    d = __ffma2_rn(make_float2(x, x), make_float2(y, z), d);
+    e = __ffma2_rn(make_float2(y, z), make_float2(z, v2), e);
+    f = __ffma2_rn(xy, make_float2(v2, v2), f);
   }
+  // moment k = 1..12 of the survey's order (1 vx, 2 vy, 3 vz, 4 vx2, 5 vy2, 6 vz2,
+  // 7 vxvy, 8 vxvz, 9 vyvz, 10 vx v2, 11 vy v2, 12 vz v2); 0 for the padding slots
   __device__ __forceinline__ float get(int k) const {
     switch (k) {
-      case 0: return a.x;
-      case 1: return a.y;
-      case 2: return b.x;
-      case 3: return b.y;
+      case 1: return a.x;
+      case 2: return a.y;
+      case 3: return b.x;
       case 4: return c.x;
       case 5: return c.y;
-      case 6: return d.x;
-      case 7: return d.y;
-      case 8: return e.x;
-      case 9: return e.y;
-      case 10: return g.x;
-      case 11: return g.y;
-      default: return h;
+      case 6: return b.y;
+      case 7: return d.x;
+      case 8: return d.y;
+      case 9: return e.x;
+      case 10: return f.x;
+      case 11: return f.y;
+      case 12: return e.y;
+      default: return 0.0f;
     }
   }
 };
 
-// Warp sums of a group's 13 moment sums (pre- plus post-collision), by a transposing
-// butterfly: each exchange halves the values a lane carries, so 16 shuffles leave the
-// total of moment idx(lane) on lanes 2i and 2i+1.  Lanes with an even id then add that
-// total into their Kahan-compensated binary32 running sum (ks, kc) for the cell.
+template <>
+struct LaneSums<double> {
+  double m[12];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(float x, float y, float z) {
+    const float v2 = fadd(fadd(fmul(x, x), fmul(y, y)), fmul(z, z));
+    const float p[12] = {x,          y,          z,          fmul(x, x), fmul(y, y), fmul(z, z),
+                         fmul(x, y), fmul(x, z), fmul(y, z), fmul(x, v2), fmul(y, v2),
+                         fmul(z, v2)};
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m[k] = __dadd_rn(m[k], (double)p[k]);
+  }
+  __device__ __forceinline__ double get(int k) const {
+    double r = 0.0;
+#pragma unroll
+    for (int j = 0; j < 12; ++j)
+      if (k == j + 1) r = m[j];
+    return r;
+  }
+};
+
+// Warp sum of a group's lane sums by a transposing butterfly over 16 slots (moments
+// 1..12 and zero padding): each exchange halves the values a lane carries, so 16
+// shuffles leave the total of moment moment_of_lane(lane) on lanes 2i and 2i+1.
 __device__ __forceinline__ int moment_of_lane(int lane) {
   return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
-__device__ __forceinline__ void reduce_moments(const Moments& m, float& ks, float& kc,
-                                               int lane) {
-  float v[16];
+template <typename T>
+__device__ __forceinline__ T group_total(const LaneSums<T>& m, int lane) {
+  T v[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = (k < kNMom) ? m.get(k) : 0.0f;
+  for (int k = 0; k < 16; ++k) v[k] = m.get(k);
 #pragma unroll
   for (int half = 8, mask = 16; half >= 1; half >>= 1, mask >>= 1) {
     const bool upper = (lane & mask) != 0;
 #pragma unroll
     for (int k = 0; k < half; ++k) {
-      const float send = upper ? v[k] : v[k + half];
-      const float keep = upper ? v[k + half] : v[k];
+      const T send = upper ? v[k] : v[k + half];
+      const T keep = upper ? v[k + half] : v[k];
       v[k] = keep + __shfl_xor_sync(kFull, send, mask);
     }
   }
-  const float tot = v[0] + __shfl_xor_sync(kFull, v[0], 1);
-  if ((lane & 1) == 0 && moment_of_lane(lane) < kNMom) {
-    const float yk = fsub(tot, kc);
-    const float t = fadd(ks, yk);
-    kc = fsub(fsub(t, ks), yk);
-    ks = t;
-  }
+  return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
-// The warp's results for one cell, added into the CTA's slots of that cell (once per
-// warp that worked on the cell).
-__device__ __forceinline__ void flush_cell(float gmax, unsigned long long cand,
-                                           unsigned long long accn, float& ks, float& kc,
-                                           bool sample, unsigned* cgmax,
-                                           unsigned long long* ccand, unsigned long long* caccn,
-                                           double* cacc, int lane) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
-    accn += __shfl_xor_sync(kFull, accn, o);
+// Exact, order-independent combination of group totals.  A cell's group totals are
+// rounded to integer multiples of a grid 2^-(41 - e), e = bit length of the cell's
+// particle count nc, and the integers added in 64 bits: integer addition does not
+// depend on the order in which warps finish their groups, so a step's cell sums are a
+// pure function of the state.  With |v| <= 101 (|each product| <= 2^20) a group total is
+// at most 2 n_g 2^20 in magnitude and the cell's integer sum stays below 2^62.  The
+// rounding adds at most 2^-(42 - e) per group total.
+__device__ __forceinline__ int grid_exponent(int nc) { return 41 - (32 - __clz(nc)); }
+
+__device__ __forceinline__ long long fixed_of(float t, int gexp) {
+  return __float2ll_rn(fmul(t, __int_as_float((127 + gexp) << 23)));
+}
+__device__ __forceinline__ long long fixed_of(double t, int gexp) {
+  return __double2ll_rn(__dmul_rn(t, __longlong_as_double((long long)(1023 + gexp) << 52)));
+}
+
+// Adds a group's results into the CTA's slots of its cell: the 12 moment totals as
+// fixed-point integers (lanes 2i of the butterfly), the largest relative speed, the
+// candidate and accepted-collision counts.  Returns false when a total exceeds the
+// magnitude the fixed-point range allows for the group's size.
+template <typename T>
+__device__ __forceinline__ bool add_group(const LaneSums<T>& m, bool sample, int gn, int nc,
+                                          float gmax, uint32_t M, unsigned accn,
+                                          unsigned long long* cfix, unsigned* cgmax,
+                                          unsigned long long* ccand,
+                                          unsigned long long* caccn, int lane) {
+  bool ok = true;
+  if (sample) {
+    const T tot = group_total(m, lane);
+    const int k = moment_of_lane(lane);
+    if ((lane & 1) == 0 && k >= 1 && k <= 12) {
+      const int ge = grid_exponent(nc);
+      const long long q = fixed_of(tot, ge);
+      // |q| <= 2 gn 2^20 2^ge holds for |products| <= 2^20
+      const long long lim = (long long)(2 * gn) << (20 + ge);
+      if (q > lim || q < -lim) ok = false;
+      atomicAdd(&cfix[k], (unsigned long long)q);
+    }
   }
-  if (lane == 0) {  // cand is the same on every lane: the sum of the groups' M
-    atomicMax(cgmax, __float_as_uint(gmax));  // gmax >= 0: bits order as values
-    atomicAdd(ccand, cand);
-    atomicAdd(caccn, accn);
+  const unsigned gbits = __reduce_max_sync(kFull, __float_as_uint(gmax));  // gmax >= 0
+  const unsigned nacc = __reduce_add_sync(kFull, accn);
+  if (lane == 0) {
+    atomicMax(cgmax, gbits);
+    atomicAdd(ccand, (unsigned long long)M);
+    atomicAdd(caccn, (unsigned long long)nacc);
   }
-  if (sample && (lane & 1) == 0 && moment_of_lane(lane) < kNMom)
-    atomicAdd(&cacc[moment_of_lane(lane)], 0.5 * ((double)ks - (double)kc));
-  ks = 0.0f;
-  kc = 0.0f;
-  __syncwarp();
+  return ok;
 }
 
 }  // namespace
@@ -219,9 +268,15 @@ __device__ __forceinline__ const InstParams& stage_instance(const InstParams& on
 // (sigma g independent of g).  CTAs per SM the register budget is set for: 3 of 8 warps,
 // 6 of 4 warps; the batched 4-warp kernel reads its parameters from shared memory and
 // spills at 6 (85 registers), so it is given 5 (no spills, 10 % faster on the
-// 256-instance batch).
-template <bool kBatch, int kWarps>
-__global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ? 5 : 6))
+// 256-instance batch).  The binary64 moment sums (kF64) hold twelve binary64 values per
+// lane and get half the CTAs per SM.
+template <bool kBatch, int kWarps, bool kF64>
+constexpr int collide_ctas_per_sm() {
+  return (kWarps == kAWarps ? 3 : (kBatch ? 5 : 6)) / (kF64 ? 2 : 1);
+}
+
+template <bool kBatch, int kWarps, bool kF64>
+__global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWarps, kF64>()))
     k_collide_move(float4* __restrict__ P, const int* __restrict__ off_all,
                    const float* __restrict__ smax_in_all, float* __restrict__ smax_out_all,
                    unsigned long long* __restrict__ ncand_all,
@@ -253,8 +308,10 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
   const int G = a.G;
   const int R = SL.rows;
   const StepSmem L = step_smem_layout(n_cells, cps, cap, kWarps, R);
+  using Acc = typename std::conditional<kF64, double, float>::type;
   int* h = reinterpret_cast<int*>(smem + L.hist);
-  double* cacc = reinterpret_cast<double*>(smem + L.cell_acc);
+  // per local cell: fixed-point moment sums (slot 0 unused), in a cell's grid
+  unsigned long long* cfix = reinterpret_cast<unsigned long long*>(smem + L.cell_acc);
   unsigned long long* ccand = reinterpret_cast<unsigned long long*>(smem + L.cell_cand);
   unsigned long long* caccn = reinterpret_cast<unsigned long long*>(smem + L.cell_accn);
   unsigned* cgmax = reinterpret_cast<unsigned*>(smem + L.cell_gmax);
@@ -289,7 +346,7 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
     return;
   }
 
-  for (int i = threadIdx.x; i < cps * kNMom; i += blockDim.x) cacc[i] = 0.0;
+  for (int i = threadIdx.x; i < cps * kNMom; i += blockDim.x) cfix[i] = 0ull;
   for (int i = threadIdx.x; i < cps; i += blockDim.x) {
     ccand[i] = 0;
     caccn[i] = 0;
@@ -323,12 +380,8 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
   const int n_groups = gfirst[c1 - c0];
 
   bool bad_bounce = false, cand_fail = false, timeout = false;
-  bool inflow_fail = false;
+  bool inflow_fail = false, mom_range = false;
   uint32_t parity = 0;
-  int cur = -1;  // local cell the warp is gathering results for
-  float gmax = 0.0f;
-  unsigned long long lcand = 0, laccn = 0;
-  float ks = 0.0f, kc = 0.0f;  // this lane's compensated moment sum of the cell
   // Groups are handed out by a counter; each warp reserves its next group one step
   // ahead and prefetches its records into L2 while it works on the current one.
   int q_next = 0;
@@ -366,15 +419,6 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
       mbar_arrive_expect_tx(bar, (uint32_t)gn * 16u);
       bulk_load(rec, P + gs, (uint32_t)gn * 16u, bar);
     }
-    if (lc != cur) {  // results so far belong to another cell
-      if (cur >= 0)
-        flush_cell(gmax, lcand, laccn, ks, kc, sample, &cgmax[cur], &ccand[cur],
-                   &caccn[cur], cacc + (size_t)cur * kNMom, lane);
-      cur = lc;
-      gmax = 0.0f;
-      lcand = 0;
-      laccn = 0;
-    }
     const float smax = smax_in[c];
     if (!mbar_wait(bar, parity)) {
       timeout = true;
@@ -384,7 +428,10 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
     parity ^= 1u;
 
     // 2. Moments before the collisions.
-    Moments m;
+    float gmax = 0.0f;
+    unsigned laccn = 0;
+    uint32_t M = 0;
+    LaneSums<Acc> m;
     m.zero();
     if (sample)
 #pragma unroll kMoveUnroll
@@ -400,14 +447,13 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
       const float mf = fmul(fmul(t1, a.coef), smax);
       const float fl = floorf(mf);
       const float frac = fsub(mf, fl);
-      uint32_t M = (uint32_t)fl;
+      M = (uint32_t)fl;
       const U4 r = philox_rk(0xffffffffu, (uint32_t)c, step, c3, a.keys);
       if (u01(r.x) < frac) M += 1;
       if (!(mf <= kMaxCandidates)) {
         M = 0;
         cand_fail = true;
       }
-      lcand += M;
       for (uint32_t kb = 0; kb < M; kb += 32) {
         const uint32_t k = kb + (uint32_t)lane;
         bool pend = k < M;
@@ -512,16 +558,16 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
     }
     __syncwarp();
     for (int i = lane; i < n_wall; i += 32) touch[i] = 0u;
-    if (sample) reduce_moments(m, ks, kc, lane);
+    if (!add_group(m, sample, gn, nc, gmax, M, laccn, cfix + (size_t)lc * kNMom, &cgmax[lc],
+                   &ccand[lc], &caccn[lc], lane))
+      mom_range = true;
     __syncwarp();
   }
-  if (cur >= 0)
-    flush_cell(gmax, lcand, laccn, ks, kc, sample, &cgmax[cur], &ccand[cur],
-               &caccn[cur], cacc + (size_t)cur * kNMom, lane);
   if (bad_bounce) atomicOr(err, kErrBounces);
   if (cand_fail && lane == 0) atomicOr(err, kErrCandidates);
   if (timeout && lane == 0) atomicOr(err, kErrCopyTimeout);
   if (inflow_fail) atomicOr(err, kErrInflow);
+  if (mom_range) atomicOr(err, kErrMoments);
   __syncthreads();
 
   for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) row[i] = h[i];
@@ -532,8 +578,15 @@ __global__ void __launch_bounds__(kWarps * 32, kWarps == kAWarps ? 3 : (kBatch ?
     smax_out[c] = fmaxf(smax_in[c], sg);
     ncand[c] += ccand[lc];
     nacc[c] += caccn[lc];
-    if (sample)
-      for (int k = 0; k < kNMom; ++k) acc[(size_t)c * kNMom + k] += cacc[lc * kNMom + k];
+    if (sample) {
+      // count: half before and half after the collisions of every particle of the cell
+      const int nc = off[c + 1] - off[c];
+      acc[(size_t)c * kNMom] += (double)nc;
+      const double grid = __longlong_as_double((long long)(1023 - grid_exponent(nc > 0 ? nc : 1)) << 52);
+      for (int k = 1; k < kNMom; ++k)
+        acc[(size_t)c * kNMom + k] +=
+            0.5 * grid * (double)(long long)cfix[(size_t)lc * kNMom + k];
+    }
   }
 }
 
@@ -889,21 +942,29 @@ cudaError_t launch_collide_move(float4* P, const int* off, const float* smax_in,
   const int warps = small ? kAWarpsSmall : kAWarps;
   const StepSmem S = step_smem_layout(L.max_cells, L.max_cps, L.max_cap, warps, L.rows);
   const dim3 block(warps * 32);
-#define DSMC_COLLIDE(B, W)                                                                   \
-  k_collide_move<B, W><<<L.n_spans_total, block, S.total, st>>>(P, off, smax_in, smax_out, \
-                                                                ncand, nacc, acc, hist, one, \
-                                                                L, err)
+#define DSMC_COLLIDE(B, W, D)                                                       \
+  k_collide_move<B, W, D><<<L.n_spans_total, block, S.total, st>>>(               \
+      P, off, smax_in, smax_out, ncand, nacc, acc, hist, one, L, err)
+#define DSMC_COLLIDE_SHAPE(B, D)   \
+  do {                             \
+    if (small)                     \
+      DSMC_COLLIDE(B, kAWarpsSmall, D); \
+    else                           \
+      DSMC_COLLIDE(B, kAWarps, D); \
+  } while (0)
+  const bool f64 = L.accum == DSMC_ACCUM_FP64;
   if (L.n_inst == 1) {
-    if (small)
-      DSMC_COLLIDE(false, kAWarpsSmall);
+    if (f64)
+      DSMC_COLLIDE_SHAPE(false, true);
     else
-      DSMC_COLLIDE(false, kAWarps);
+      DSMC_COLLIDE_SHAPE(false, false);
   } else {
-    if (small)
-      DSMC_COLLIDE(true, kAWarpsSmall);
+    if (f64)
+      DSMC_COLLIDE_SHAPE(true, true);
     else
-      DSMC_COLLIDE(true, kAWarps);
+      DSMC_COLLIDE_SHAPE(true, false);
   }
+#undef DSMC_COLLIDE_SHAPE
 #undef DSMC_COLLIDE
   return cudaGetLastError();
 }
@@ -997,10 +1058,14 @@ cudaError_t launch_pack(const float* y, const float* vx, const float* vy, const 
 }
 
 cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes) {
-  const void* collide[4] = {(const void*)k_collide_move<false, kAWarps>,
-                            (const void*)k_collide_move<true, kAWarps>,
-                            (const void*)k_collide_move<false, kAWarpsSmall>,
-                            (const void*)k_collide_move<true, kAWarpsSmall>};
+  const void* collide[8] = {(const void*)k_collide_move<false, kAWarps, false>,
+                            (const void*)k_collide_move<true, kAWarps, false>,
+                            (const void*)k_collide_move<false, kAWarpsSmall, false>,
+                            (const void*)k_collide_move<true, kAWarpsSmall, false>,
+                            (const void*)k_collide_move<false, kAWarps, true>,
+                            (const void*)k_collide_move<true, kAWarps, true>,
+                            (const void*)k_collide_move<false, kAWarpsSmall, true>,
+                            (const void*)k_collide_move<true, kAWarpsSmall, true>};
   for (const void* f : collide) {
     const cudaError_t e =
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a_bytes);

@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("collisions", ctypes.c_int), ("profile", ctypes.c_int),
                 ("span_particles", ctypes.c_int), ("cta_warps", ctypes.c_int),
                 ("span_rows", ctypes.c_int), ("graph", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("accum", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -145,6 +145,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dsmc_step": (st, [H, c.c_int]),
         "dsmc_sync": (st, [H]),
         "dsmc_sample_moments": (st, [H, c.c_void_p, c.POINTER(c.c_longlong)]),
+        "dsmc_cell_fields": (st, [c.c_void_p, c.c_longlong, c.c_int, c.c_int, c.c_void_p]),
+        "dsmc_cell_fields_of": (st, [H, c.c_int, c.c_void_p]),
         "dsmc_reset_samples": (st, [H]),
         "dsmc_copy_state": (st, [H, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
         "dsmc_copy_cells": (st, [H, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
@@ -260,7 +262,7 @@ class Dsmc:
                  dt_factor: float = 0.2, dt: float = 0.0, sample_start: int = 0,
                  group_size: int = 256, collisions: bool = True, profile: bool = False,
                  span_particles: int = 0, cta_warps: int = 0, span_rows: int = 0,
-                 graph: bool = False, stream=None, workspace: str = "torch",
+                 graph: bool = False, accum: int = 0, stream=None, workspace: str = "torch",
                  gas: Optional[dict] = None):
         L = load_library()
         self._lib = L
@@ -273,7 +275,7 @@ class Dsmc:
         o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
         o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
         o.span_particles, o.cta_warps, o.graph = int(span_particles), int(cta_warps), int(bool(graph))
-        o.span_rows = int(span_rows)
+        o.span_rows, o.accum = int(span_rows), int(accum)
         self._ws = None
         if workspace == "torch":
             import torch
@@ -343,6 +345,13 @@ class Dsmc:
     def reset_samples(self) -> None:
         _check(self._lib.dsmc_reset_samples(self._h))
 
+    def fields(self) -> dict:
+        """Cell fields of the samples so far, computed by the library on the device
+        (see ``fields``)."""
+        out = np.empty((self.n_cells, NFIELD), np.float64)
+        _check(self._lib.dsmc_cell_fields_of(self._h, 0, _ptr(out)))
+        return _field_dict(out)
+
     def state(self):
         arrs = [np.empty(self.N, np.float32) for _ in range(4)]
         _check(self._lib.dsmc_copy_state(self._h, *[_ptr(a) for a in arrs]))
@@ -404,12 +413,13 @@ def make_instance(Kn: float, n_cells: int, ppc: int, *, omega: float = 0.5,
 
 
 def _options(dt_factor=0.2, dt=0.0, sample_start=0, group_size=256, collisions=True,
-             profile=False, span_particles=0, cta_warps=0, span_rows=0, graph=False) -> Options:
+             profile=False, span_particles=0, cta_warps=0, span_rows=0, graph=False,
+             accum=0) -> Options:
     o = default_options()
     o.dt_factor, o.dt, o.sample_start = float(dt_factor), float(dt), int(sample_start)
     o.group_size, o.collisions, o.profile = int(group_size), int(bool(collisions)), int(bool(profile))
     o.span_particles, o.cta_warps, o.graph = int(span_particles), int(cta_warps), int(bool(graph))
-    o.span_rows = int(span_rows)
+    o.span_rows, o.accum = int(span_rows), int(accum)
     return o
 
 
@@ -500,6 +510,12 @@ class _Multi:
         ns = ctypes.c_longlong()
         _check(self._lib.dsmc_sample_moments_of(self._h, int(i), _ptr(out), ctypes.byref(ns)))
         return out, int(ns.value)
+
+    def fields(self, i: int) -> dict:
+        """Cell fields of instance i's samples (``dsmc_cell_fields_of``)."""
+        out = np.empty((self.info(i)["n_cells"], NFIELD), np.float64)
+        _check(self._lib.dsmc_cell_fields_of(self._h, int(i), _ptr(out)))
+        return _field_dict(out)
 
     def channel_sums(self):
         """[id bound, 2]: sampled particle count and sum of vx per instance id."""
@@ -857,28 +873,21 @@ def surrogate_exponents(Kn: float):
     return tuple(float(x) for x in b)
 
 
+FIELD_NAMES = ("n", "ux", "uy", "uz", "T", "Pxy", "qx", "qy", "qz")
+NFIELD = len(FIELD_NAMES)
+
+
+def _field_dict(out: np.ndarray) -> dict:
+    return {k: out[:, i].copy() for i, k in enumerate(FIELD_NAMES)}
+
+
 def fields(acc, n_samples: int, ppc: int) -> dict:
-    """Cell fields from raw sums: relative density n, velocity (v0), temperature (T0),
-    shear stress P_xy (P0; rho / P0 = 2 / v0^2 in the units of Eq. 6) and heat flux
-    (P0 v0), from central moments of the sampled velocities."""
-    a = np.asarray(acc, np.float64)
-    cnt = a[:, 0]
-    with np.errstate(invalid="ignore", divide="ignore"):
-        mean = a[:, 1:4] / cnt[:, None]
-        second = np.empty((a.shape[0], 3, 3))
-        idx = {(0, 0): 4, (1, 1): 5, (2, 2): 6, (0, 1): 7, (0, 2): 8, (1, 2): 9}
-        for (i, j), k in idx.items():
-            second[:, i, j] = second[:, j, i] = a[:, k] / cnt
-        third = a[:, 10:13] / cnt[:, None]  # <v_i |v|^2>
-        rel_n = cnt / (n_samples * ppc)
-        cov = second - mean[:, :, None] * mean[:, None, :]  # <c_i c_j>
-        csq = np.trace(cov, axis1=1, axis2=2)
-        msq = (mean ** 2).sum(1)
-        vsq = np.trace(second, axis1=1, axis2=2)
-        # <c_i |c|^2> expanded in raw moments
-        q_raw = (third - 2.0 * np.einsum("nij,nj->ni", second, mean)
-                 - mean * vsq[:, None] + 2.0 * mean * msq[:, None])
-    return {"n": rel_n, "ux": mean[:, 0], "uy": mean[:, 1], "uz": mean[:, 2],
-            "T": (2.0 / 3.0) * csq, "Pxy": 2.0 * rel_n * cov[:, 0, 1],
-            "qx": rel_n * q_raw[:, 0], "qy": rel_n * q_raw[:, 1]}
+    """Cell fields from raw sums (``dsmc_cell_fields``): relative density n, velocity
+    (v0), temperature (T0), shear stress P_xy (P0) and heat flux (P0 v0), one array per
+    name of ``FIELD_NAMES``."""
+    a = np.ascontiguousarray(acc, np.float64)
+    out = np.empty((a.shape[0], NFIELD), np.float64)
+    _check(load_library().dsmc_cell_fields(_ptr(a), int(n_samples), int(ppc), a.shape[0],
+                                           _ptr(out)))
+    return _field_dict(out)
 

@@ -44,8 +44,11 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_options(lib):
     o = D.default_options()
     assert (o.dt_factor, o.dt, o.sample_start, o.group_size, o.collisions, o.profile,
-            o.span_particles, o.cta_warps, o.span_rows, o.graph) == \
-        (0.2, 0.0, 0, 256, 1, 0, 0, 0, 0, 0)
+            o.span_particles, o.cta_warps, o.span_rows, o.graph, o.accum) == \
+        (0.2, 0.0, 0, 256, 1, 0, 0, 0, 0, 0, 0)
+    # the ctypes mirror of dsmc_options has the C struct's size (accum sits in what was
+    # the padding before the stream pointer)
+    assert ctypes.sizeof(D.Options) == 64 and D.Options.accum.offset == 52
     assert lib.dsmc_kernel_count() == 7
     assert lib.dsmc_kernel_name(0) == b"init"
     assert lib.dsmc_status_string(4) == b"device limit reached"
@@ -87,7 +90,8 @@ def test_bad_gas_and_options_rejected(lib):
     assert st == 1 and "mass" in msg
     for field, val in (("group_size", 3), ("group_size", 1024), ("dt_factor", 0.0),
                        ("dt", -1.0), ("span_particles", 1000), ("span_particles", 1 << 25),
-                       ("cta_warps", 6), ("cta_warps", 16), ("span_rows", 3), ("graph", 1)):
+                       ("cta_warps", 6), ("cta_warps", 16), ("span_rows", 3), ("graph", 1),
+                       ("accum", 2), ("accum", -1)):
         o = D.default_options()
         setattr(o, field, val)
         st, msg = _create(lib, opt=o)
@@ -236,3 +240,57 @@ def test_missing_library_fails_loudly(tmp_path):
             D.load_library(str(tmp_path / "libdsmc.so"))
     finally:
         D._lib = saved
+
+
+def _random_sums(rng, n_cells, n_samples, ppc, u=(0.01, -0.002, 0.0), P=0.003):
+    """Raw sums of a sheared Maxwellian sample: per cell, count particles with velocity
+    components N(u_i, 1/2) and a prescribed vx-vy covariance, summed as the sampler sums
+    them (plain numpy; none of the method's arithmetic)."""
+    out = np.zeros((n_cells, 13))
+    for c in range(n_cells):
+        n = n_samples * ppc + int(rng.integers(-ppc, ppc))
+        cov = np.array([[0.5, P / 2, 0.0], [P / 2, 0.5, 0.0], [0.0, 0.0, 0.5]])
+        v = rng.multivariate_normal(u, cov, size=n)
+        v2 = (v ** 2).sum(1)
+        x, y, z = v.T
+        out[c] = [n, x.sum(), y.sum(), z.sum(), (x * x).sum(), (y * y).sum(), (z * z).sum(),
+                  (x * y).sum(), (x * z).sum(), (y * z).sum(), (x * v2).sum(), (y * v2).sum(),
+                  (z * v2).sum()]
+    return out
+
+
+def test_cell_fields_match_the_oracle_definitions(lib):
+    """dsmc_cell_fields (host code of the library) against the oracle's plain numpy
+    post-processing of the same raw sums, and against values known from the sample:
+    density, mean velocity, temperature 1 (T0) of N(u, 1/2) components, shear stress
+    2 n cov(vx, vy), zero heat flux of a Gaussian."""
+    import oracle
+    rng = np.random.default_rng(7)
+    ppc, ns = 40, 25
+    acc = _random_sums(rng, 6, ns, ppc)
+    acc[3] = 0.0  # a cell that was never sampled
+    got = D.fields(acc, ns, ppc)
+    want = oracle.fields(acc, ns, ppc)
+    for k in ("n", "ux", "uy", "uz", "T", "Pxy", "qx", "qy"):
+        a, b = got[k], want[k]
+        live = np.arange(6) != 3
+        np.testing.assert_allclose(a[live], b[live], rtol=1e-12, atol=1e-15, err_msg=k)
+        if k != "n":
+            assert np.isnan(a[3]), k
+    assert got["n"][3] == 0.0
+    live = np.arange(6) != 3
+    n_total = acc[live, 0]
+    np.testing.assert_allclose(got["n"][live], n_total / (ns * ppc))
+    # statistical agreement with the sampled distribution (1,000 particles per cell)
+    assert np.all(np.abs(got["ux"][live] - 0.01) < 5 * np.sqrt(0.5 / n_total))
+    assert np.all(np.abs(got["T"][live] - 1.0) < 0.2)
+    assert np.all(np.abs(got["Pxy"][live] - 2 * got["n"][live] * 0.0015) < 0.2)
+    assert np.all(np.abs(got["qz"][live]) < 0.2)
+
+
+def test_cell_fields_reject_bad_arguments(lib):
+    out = np.zeros((2, D.NFIELD))
+    acc = np.ones((2, 13))
+    assert lib.dsmc_cell_fields(D._ptr(acc), 0, 10, 2, D._ptr(out)) == 1
+    assert lib.dsmc_cell_fields(D._ptr(acc), 5, 0, 2, D._ptr(out)) == 1
+    assert lib.dsmc_cell_fields(None, 5, 10, 2, D._ptr(out)) == 1

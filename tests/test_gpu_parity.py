@@ -3,13 +3,19 @@
 Deterministic mode: both sides draw the same Philox streams keyed on (step, slot,
 bounce) and (step, cell, group, candidate) and round every binary32 operation once,
 so particle state, cell offsets (the sort order), (sigma g)_max and collision
-counters must agree bit for bit.  The moment sums are binary64 in the oracle; the CUDA
-path adds a collision group's products in binary32 (per lane at most 24 terms: 12 before
-and 12 after the collisions, then 5 butterfly levels across the warp) and the group
-totals of a cell in compensated (Kahan) binary32 before one binary64 addition.  Each
-product thus passes through at most 24 + 5 + 2 = 31 roundings of relative size 2^-24
-on partial sums bounded by the sum of |products|, so the sums must agree within
-31 * 2^-24 * sum|product| < 2e-6 * sum|product|, with sum|product| from the oracle.
+counters must agree bit for bit.  The moment sums are binary64 in the oracle.  The CUDA
+path's default (DSMC_ACCUM_FP32) adds a collision group's products in binary32 (per lane
+at most 24 terms: 12 before and 12 after the collisions, the second and third moments
+by fused multiply-add, which skips the product's own rounding of at most half a unit;
+then 5 butterfly levels across the warp), rounds each group total to the cell's
+fixed-point grid (at most 2^-(42 - e) absolute, e the bit length of the cell's count:
+below 1e-9 of sum|product| for every cell here) and adds the integers exactly.  Each
+product thus passes through at most 23 + 0.5 + 5 = 28.5 roundings of relative size
+2^-24 on partial sums bounded by the sum of |products|, so the sums must agree within
+28.5 * 2^-24 * sum|product| + grid < 2e-6 * sum|product|, with sum|product| from the
+oracle.  DSMC_ACCUM_FP64 forms the same binary32 products and adds them in binary64:
+it differs from the oracle only by the summation order and the grid, within 1e-10 of
+sum|product| on the runs below.
 
 Statistical mode: independent seeds on each side; time-averaged velocity, shear
 stress and heat flux agree within the combined standard errors.
@@ -26,6 +32,7 @@ from paper_2311_14140_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 MOM_TOL = 2e-6
+MOM_TOL_F64 = 1e-10
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -48,7 +55,7 @@ def make_pair(omega=0.5, Kn=1.0, n_cells=100, ppc=200, F=0.0, seed=0, G=256, dt=
     return o, g
 
 
-def assert_bitexact(o, g, moments=True):
+def assert_bitexact(o, g, moments=True, mom_tol=MOM_TOL):
     for name, a, b in zip(("y", "vx", "vy", "vz"), o.state(), g.state()):
         bad = np.flatnonzero(a.view(np.uint32) != b.view(np.uint32))
         assert bad.size == 0, f"{name}: {bad.size} slots differ, first {bad[:5]}"
@@ -62,7 +69,7 @@ def assert_bitexact(o, g, moments=True):
         mo, no = o.moments()
         mg, ng = g.moments()
         assert no == ng
-        bound = MOM_TOL * o.abs_moments()
+        bound = mom_tol * o.abs_moments()
         err = np.abs(mg - mo)
         assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
 
@@ -204,18 +211,20 @@ def _oracle_run(args):
 
 def test_statistical_16_seeds():
     """Argon hard spheres at Kn = 1 (100 cells x 200 particles, 2,000 steps, last 1,000
-    sampled): 16 GPU seeds against 16 different oracle seeds.  Velocity, shear stress
-    and heat flux, averaged over 10 bins of 10 cells, agree within 3.5 combined
-    standard errors (30 comparisons), and the channel means within 3."""
-    from paper_2311_14140_gb300 import Dsmc, fields
+    sampled): 16 GPU seeds against 16 different oracle seeds.  The channel means of
+    velocity, shear stress and heat flux agree within 3 combined standard errors; the
+    same quantities averaged over 10 bins of 10 cells (a family of 30 comparisons) within
+    3.5, the per-comparison bar that keeps the family-wise false-alarm rate near 1 %
+    (Bonferroni: 30 x P(|t_30| > 3.5) = 0.045; 30 x P(|z| > 3.5) = 0.014), where 3 would
+    fail one run in ten by chance alone (30 x P(|t_30| > 3) = 0.16)."""
+    from paper_2311_14140_gb300 import Dsmc
     w = W.HS_KN1
     gpu = []
     for seed in range(16):
         g = Dsmc(w.Kn, w.n_cells, w.ppc, omega=w.omega, body_force=w.body_force, seed=seed,
                  sample_start=w.sample_start)
         g.step(w.steps)
-        acc, ns = g.moments()
-        gpu.append(fields(acc, ns, w.ppc))
+        gpu.append(g.fields())  # the library's post-processing (dsmc_cell_fields_of)
         g.close()
     with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
         cpu = pool.map(_oracle_run, [(100 + s,) for s in range(16)])
@@ -247,3 +256,49 @@ def test_full_size_vhs_50m_bitexact():
     o.step(2)
     g.step(2)
     assert_bitexact(o, g)
+
+
+@pytest.mark.parametrize("case", [
+    dict(omega=0.5, Kn=1.0, n_cells=100, ppc=200, F=8.713e-4),
+    dict(omega=0.81, Kn=0.1, n_cells=40, ppc=700, F=4.038e-4),
+])
+def test_binary64_moment_sums_against_oracle(case):
+    """options.accum = DSMC_ACCUM_FP64: the state is the same as with the default (the
+    sums never feed back), and the moment sums agree with the oracle's binary64 sums to
+    1e-10 of sum|product| after 30 sampled steps; the default binary32 sums agree with
+    both within the binary32 bound."""
+    from paper_2311_14140_gb300 import Dsmc
+    o, g = make_pair(seed=4, **case)
+    g2 = Dsmc(case["Kn"], case["n_cells"], case["ppc"], omega=case["omega"],
+              body_force=case["F"], seed=4, accum=1)
+    o.step(30)
+    g.step(30)
+    g2.step(30)
+    assert_bitexact(o, g2, mom_tol=MOM_TOL_F64)
+    m32, _ = g.moments()
+    m64, _ = g2.moments()
+    assert np.all(np.abs(m32 - m64) <= MOM_TOL * o.abs_moments())
+    for u, v in zip(g.state(), g2.state()):
+        np.testing.assert_array_equal(u.view(np.uint32), v.view(np.uint32))
+
+
+@pytest.mark.parametrize("accum", [0, 1])
+def test_moment_sums_reproducible(accum):
+    """The moment sums are a pure function of the run: two identical runs, and runs
+    with other span partitions and CTA shapes (which change which warp takes which
+    collision group, and in what order groups finish), give bit-identical sums."""
+    from paper_2311_14140_gb300 import Dsmc
+    kw = dict(omega=0.81, body_force=1e-3, seed=21, accum=accum)
+    runs = [Dsmc(0.2, 300, 900, **kw), Dsmc(0.2, 300, 900, **kw),
+            Dsmc(0.2, 300, 900, span_particles=8192, **kw),
+            Dsmc(0.2, 300, 900, cta_warps=4, span_rows=2, **kw)]
+    ref = None
+    for g in runs:
+        g.step(15)
+        m, n = g.moments()
+        if ref is None:
+            ref = (m, n)
+        else:
+            assert n == ref[1]
+            np.testing.assert_array_equal(m.view(np.uint64), ref[0].view(np.uint64))
+        g.close()

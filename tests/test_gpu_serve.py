@@ -31,11 +31,12 @@ D_ = dict(Kn=0.05, n_cells=211, ppc=55, omega=0.5, body_force=2e-3, seed=2 ** 40
 
 def vx_tol(m):
     """Tolerance of a sum of sampled vx between two runs whose states agree bit for bit:
-    the moment sums are binary32 group sums, compensated per warp, and which warp takes
-    which collision group (hence the grouping of the additions) depends on scheduling
-    and CTA shape, so sums agree to the DSMC parity bound 2e-6 * sum |vx|, with
-    sum |vx| <= sqrt(count * sum vx^2) (Cauchy-Schwarz)."""
-    return 2e-6 * np.sqrt(m[:, 0].sum() * m[:, 4].sum())
+    their per-cell sums are then bit-identical (group totals combine exactly, whatever
+    warp takes which group), and only the order in which the cells' binary64 sums are
+    added into the channel total differs (the device's reduction against numpy's), so the
+    totals agree to 1e-12 * sum |vx|, with sum |vx| <= sqrt(count * sum vx^2)
+    (Cauchy-Schwarz)."""
+    return 1e-12 * np.sqrt(m[:, 0].sum() * m[:, 4].sum())
 
 
 def alone(d, steps, **kw):
@@ -142,6 +143,5 @@ def test_solve_alone_matches_serving_one_request():
                  max_cells_per_instance=400, sample_start=8)
     r = p.serve([req], epoch_steps=16, batches=4)[0]
     assert s["steps"] == r["steps"] and s["count"] == r["count"]
-    # as vx_tol, with sum |vx| below the count (thermal speeds ~N(0, 1/2) in v0 units and
-    # a drift far below 1 give sum |vx| ~ 0.4 count)
-    assert abs(s["sum_vx"] - r["sum_vx"]) <= 2e-6 * s["count"]
+    # the same per-cell sums reduced over the instance's cells by the same kernel
+    assert s["sum_vx"] == r["sum_vx"]
