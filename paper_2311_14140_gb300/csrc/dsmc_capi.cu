@@ -495,6 +495,7 @@ InstParams instance_params(const dsmc_sim* h, int id, int span_base) {
   a.vexp = x.p.vexp;
   a.vinv = x.p.vinv;
   a.lncv = x.p.lncv;
+  a.lg2cv = (float)std::log2((double)x.p.cvhs);
   a.k0 = (uint32_t)(x.seed & 0xffffffffu);
   a.k1 = (uint32_t)(x.seed >> 32);
   for (int r = 0; r < 10; ++r) {

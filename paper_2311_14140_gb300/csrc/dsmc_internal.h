@@ -92,6 +92,7 @@ struct InstParams {
   float coef;              // n sigma_ref dt / (2 ppc)
   float cvhs, vexp, vinv;  // VHS factor, exponent 2 - 2 omega and its inverse
   float lncv;              // ln cvhs
+  float lg2cv;             // log2 cvhs (for the bracketing approximation of the threshold)
   uint32_t k0, k1;         // Philox key (seed)
   PhiloxKeys keys;         // the ten round keys of that key
   long long step0;         // the instance's step k runs at global step step0 + k
@@ -106,7 +107,8 @@ struct InstParams {
 
 // Dynamic shared memory of one collide/move CTA (byte offsets).
 struct StepSmem {
-  size_t hist, cell_acc, cell_cand, cell_accn, cell_gmax, cell_groups, warps, per_warp, total;
+  size_t hist, cell_acc, cell_cand, cell_accn, cell_gmax, cell_groups, cell_start, cell_smax,
+      warps, per_warp, total;
   size_t w_rec, w_own, w_bar;  // offsets inside one warp's area
 };
 
@@ -127,7 +129,11 @@ __host__ __device__ inline StepSmem step_smem_layout(int n_cells, int cps, int c
   L.cell_gmax = o;
   o += (size_t)cps * 4;
   L.cell_groups = o;  // group prefix of the span's cells (cps + 1) and a counter
-  o = step_align(o + ((size_t)cps + 2) * 4, 128);
+  o += ((size_t)cps + 2) * 4;
+  L.cell_start = o;  // first slot of each of the span's cells and the end (cps + 1)
+  o += ((size_t)cps + 1) * 4;
+  L.cell_smax = o;  // (sigma g)_max of the span's cells at the step's start
+  o = step_align(o + (size_t)cps * 4, 128);
   // per warp: the group's records (cap float4, written by a bulk copy), an owner word
   // per particle (reused as the queue of wall hits), and an mbarrier
   size_t w = 0;

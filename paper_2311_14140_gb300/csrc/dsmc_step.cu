@@ -72,6 +72,29 @@ __device__ __forceinline__ void sincos_turn(float v, float& sn, float& cs) {
   }
 }
 
+// VHS acceptance threshold on the relative speed (sigma g > u (sigma g)_max written as
+// g > thr): thr = exp((ln(u smax) - ln cvhs) / (2 - 2 omega)), with the library's own
+// binary32 ln and exp; this value decides.
+__device__ __forceinline__ float vhs_threshold(float us, float vinv, float lncv) {
+  return exp32(fmul(vinv, fsub(ln32(us), lncv)));
+}
+
+// The same threshold from the hardware's base-2 approximations: within 3e-5 relative of
+// vhs_threshold (the approximations' own errors, the binary32 rounding of an argument of
+// magnitude below 70, and the 2-ulp error of ln32 and exp32).  [t (1 - 2^-10),
+// t (1 + 2^-10)] therefore brackets the deciding value; a relative speed outside the
+// bracket is decided without it.
+constexpr float kThrLo = 1.0f - 0x1p-10f;
+constexpr float kThrHi = 1.0f + 0x1p-10f;
+
+__device__ __forceinline__ float vhs_threshold_approx(float us, float vinv, float lg2cv) {
+  float l, t;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(us));
+  const float x = fmul(vinv, fsub(l, lg2cv));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(x));
+  return t;
+}
+
 // Isotropic scattering direction from two uniform words by the cylindrical (Archimedes)
 // map: n_z = 2 u(w0) - 1 and azimuth 2 pi u(w1), independent and uniform, give
 // n = (sqrt(1 - n_z^2) cos, sqrt(1 - n_z^2) sin, n_z), uniform on the sphere.  No
@@ -309,7 +332,7 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
   const int R = SL.rows;
   const StepSmem L = step_smem_layout(n_cells, cps, cap, kWarps, R);
   using Acc = typename std::conditional<kF64, double, float>::type;
-  int* h = reinterpret_cast<int*>(smem + L.hist);
+  int* h = reinterpret_cast<int*>(smem + L.hist);  // the span's rows x n_cells counts
   // per local cell: fixed-point moment sums (slot 0 unused), in a cell's grid
   unsigned long long* cfix = reinterpret_cast<unsigned long long*>(smem + L.cell_acc);
   unsigned long long* ccand = reinterpret_cast<unsigned long long*>(smem + L.cell_cand);
@@ -317,6 +340,8 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
   unsigned* cgmax = reinterpret_cast<unsigned*>(smem + L.cell_gmax);
   int* gfirst = reinterpret_cast<int*>(smem + L.cell_groups);  // cps + 1 group prefix
   int* next_group = gfirst + cps + 1;
+  int* cstart = reinterpret_cast<int*>(smem + L.cell_start);     // cps + 1 cell starts
+  float* csmax = reinterpret_cast<float*>(smem + L.cell_smax);   // cps (sigma g)_max
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   unsigned char* wmem = smem + L.warps + (size_t)wib * L.per_warp;
@@ -333,16 +358,21 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
   const unsigned lt = (1u << lane) - 1u;
   // rows (span R + r) of the sort matrix; row r counts the r-th half of the slots
   int* row = hist + a.hist_base + (size_t)span * R * n_cells;
-  for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) h[i] = 0;
   const int sb0 = off[c0], sb1 = off[c1];
   const int mid = (R > 1) ? sb0 + ((sb1 - sb0) >> 1) : sb1;  // first slot of the second row
+  for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) h[i] = 0;
+  // count one particle of slot p in new cell cn
+  auto count_cell = [&](int p, int cn) { atomicAdd(&h[(p >= mid ? n_cells : 0) + cn], 1); };
+  auto write_rows = [&]() {
+    for (int e = threadIdx.x; e < R * n_cells; e += blockDim.x) row[e] = h[e];
+  };
 
   if (count_only) {  // sort into cells: count the cells of the span's slots
     __syncthreads();
     for (int p = sb0 + threadIdx.x; p < sb1; p += blockDim.x)
-      atomicAdd(&h[(p >= mid ? n_cells : 0) + cell_of(P[p].x, n_cells, a.ncf)], 1);
+      count_cell(p, cell_of(P[p].x, n_cells, a.ncf));
     __syncthreads();
-    for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) row[i] = h[i];
+    write_rows();
     return;
   }
 
@@ -356,7 +386,13 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
     int base = 0;
     for (int i0 = 0; i0 < c1 - c0; i0 += 32) {
       const int i = i0 + lane;
-      const int g = (i < c1 - c0) ? group_count(off[c0 + i + 1] - off[c0 + i], G) : 0;
+      int g = 0;
+      if (i < c1 - c0) {
+        const int s0 = off[c0 + i], s1 = off[c0 + i + 1];
+        g = group_count(s1 - s0, G);
+        cstart[i] = s0;
+        csmax[i] = smax_in[c0 + i];
+      }
       int incl = g;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -368,6 +404,7 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
     }
     if (lane == 0) {
       gfirst[c1 - c0] = base;
+      cstart[c1 - c0] = off[c1];
       *next_group = 0;
     }
   }
@@ -382,44 +419,59 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
   bool bad_bounce = false, cand_fail = false, timeout = false;
   bool inflow_fail = false, mom_range = false;
   uint32_t parity = 0;
-  // Groups are handed out by a counter; each warp reserves its next group one step
-  // ahead and prefetches its records into L2 while it works on the current one.
-  int q_next = 0;
-  if (lane == 0) q_next = atomicAdd(next_group, 1);
-  q_next = __shfl_sync(kFull, q_next, 0);
-  for (;;) {
-    const int q = q_next;
-    if (q >= n_groups) break;
-    int lc = 0;
-    while (gfirst[lc + 1] <= q) ++lc;
-    const int c = c0 + lc;
-    const int gi = q - gfirst[lc];
-    const int start = off[c];
-    const int nc = off[c + 1] - start;
-    const int ng = gfirst[lc + 1] - gfirst[lc];
-    const int gs = start + gi * G;
-    const int gn = (gi == ng - 1) ? nc - gi * G : G;
-    if (lane == 0) q_next = atomicAdd(next_group, 1);
-    q_next = __shfl_sync(kFull, q_next, 0);
-    if (q_next < n_groups && lane == 0) {
-      int ln = lc;
-      while (gfirst[ln + 1] <= q_next) ++ln;
-      const int cn = c0 + ln;
-      const int gin = q_next - gfirst[ln];
-      const int ncn = off[cn + 1] - off[cn];
-      const int ngn = gfirst[ln + 1] - gfirst[ln];
-      const int gnn = (gin == ngn - 1) ? ncn - gin * G : G;
-      bulk_prefetch_l2(P + off[cn] + gin * G, (uint32_t)gnn * 16u);
-    }
-
-    // 1. Bulk copy of the group's records into shared memory (one lane issues it).
+  // Groups are handed out by a counter.  Each warp reserves its next group when it
+  // starts one, prefetches the next group's records into L2, and issues their bulk copy
+  // into its buffer as soon as the current group's records have been read for the last
+  // time.  A group is described from shared memory alone (cell starts and group prefix).
+  auto cell_of_group = [&](int q, int from) {
+    int l = from;
+    while (gfirst[l + 1] <= q) ++l;
+    return l;
+  };
+  auto group_slots = [&](int q, int l, int& gs_, int& gn_) {
+    const int gi_ = q - gfirst[l];
+    const int nc_ = cstart[l + 1] - cstart[l];
+    gs_ = cstart[l] + gi_ * G;
+    gn_ = (gi_ == gfirst[l + 1] - gfirst[l] - 1) ? nc_ - gi_ * G : G;
+  };
+  auto issue_copy = [&](int gs_, int gn_) {
     fence_proxy_async_smem();  // earlier generic accesses to rec before the async write
     __syncwarp();
     if (lane == 0) {
-      mbar_arrive_expect_tx(bar, (uint32_t)gn * 16u);
-      bulk_load(rec, P + gs, (uint32_t)gn * 16u, bar);
+      mbar_arrive_expect_tx(bar, (uint32_t)gn_ * 16u);
+      bulk_load(rec, P + gs_, (uint32_t)gn_ * 16u, bar);
     }
-    const float smax = smax_in[c];
+  };
+  int q_next = 0;
+  if (lane == 0) q_next = atomicAdd(next_group, 1);
+  q_next = __shfl_sync(kFull, q_next, 0);
+  int l_next = 0;
+  if (q_next < n_groups) {
+    int s_, n_;
+    l_next = cell_of_group(q_next, 0);
+    group_slots(q_next, l_next, s_, n_);
+    issue_copy(s_, n_);
+  }
+  for (;;) {
+    const int q = q_next;
+    if (q >= n_groups) break;
+    const int lc = l_next;
+    const int c = c0 + lc;
+    const int gi = q - gfirst[lc];
+    const int nc = cstart[lc + 1] - cstart[lc];
+    int gs, gn;
+    group_slots(q, lc, gs, gn);
+    if (lane == 0) q_next = atomicAdd(next_group, 1);
+    q_next = __shfl_sync(kFull, q_next, 0);
+    int gs_next = 0, gn_next = 0;
+    if (q_next < n_groups) {
+      l_next = cell_of_group(q_next, lc);
+      group_slots(q_next, l_next, gs_next, gn_next);
+      if (lane == 0) bulk_prefetch_l2(P + gs_next, (uint32_t)gn_next * 16u);
+    }
+
+    // 1. The group's records in shared memory (bulk copy issued beforehand).
+    const float smax = csmax[lc];
     if (!mbar_wait(bar, parity)) {
       timeout = true;
       mbar_wait(bar, parity);  // give the copy one more bounded chance to land
@@ -447,34 +499,50 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
       const float mf = fmul(fmul(t1, a.coef), smax);
       const float fl = floorf(mf);
       const float frac = fsub(mf, fl);
-      M = (uint32_t)fl;
-      const U4 r = philox_rk(0xffffffffu, (uint32_t)c, step, c3, a.keys);
-      if (u01(r.x) < frac) M += 1;
-      if (!(mf <= kMaxCandidates)) {
-        M = 0;
-        cand_fail = true;
-      }
-      for (uint32_t kb = 0; kb < M; kb += 32) {
-        const uint32_t k = kb + (uint32_t)lane;
-        bool pend = k < M;
+      const bool mbad = !(mf <= kMaxCandidates);
+      if (mbad) cand_fail = true;
+      // M is floor(mf) or floor(mf) + 1 by the count-rounding draw (candidate counter
+      // 0xffffffff).  Batch 0 draws it on lane 31 beside candidates 0..30 on lanes
+      // 0..30; later batches hold candidates 31 + 32 b + lane.
+      for (uint32_t kb = 0, first = 1;; first = 0) {
+        const uint32_t k =
+            first ? (lane == 31 ? 0xffffffffu : (uint32_t)lane) : kb + (uint32_t)lane;
+        U4 w{};
+        if (first) {
+          w = philox_rk(k, (uint32_t)c, step, c3, a.keys);
+          const float ur = __shfl_sync(kFull, u01(w.x), 31);
+          M = mbad ? 0u : (uint32_t)fl + (ur < frac ? 1u : 0u);
+        }
+        bool pend = first ? (lane < 31 && (uint32_t)lane < M) : (k < M);
+        if (M == 0u) break;
         int i = 0, j = 0;
-        float thr = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
+        // acceptance: g > thr; thr_lo <= thr <= thr_hi, equal unless the VHS threshold
+        // was bracketed by the fast approximation (thr itself is then formed only for
+        // a relative speed inside the bracket)
+        float us = 0.0f, thr_lo = 0.0f, thr_hi = 0.0f, nx = 0.0f, ny = 0.0f, nz = 0.0f;
         if (pend) {
           // one draw per candidate: word 0 the pair (multiply-shift: i from the high
           // half of w0 gn, j from the low half times gn - 1), word 1 the acceptance
           // uniform, words 2 and 3 the scattering direction
-          const U4 w = philox_rk(k, (uint32_t)c, step, c3, a.keys);
+          if (!first) w = philox_rk(k, (uint32_t)c, step, c3, a.keys);
           const unsigned long long pij = (unsigned long long)w.x * (unsigned long long)gn;
           i = (int)(pij >> 32);
           j = (int)__umulhi((uint32_t)pij, (uint32_t)(gn - 1));
           j += (j >= i) ? 1 : 0;
-          const float us = fmul(u01(w.y), smax);
-          if (mode == 0)
-            thr = us;
-          else if (mode == 1)
-            thr = exp32(fmul(a.vinv, fsub(ln32(us), a.lncv)));
-          else
-            thr = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
+          us = fmul(u01(w.y), smax);
+          if (mode == 0) {
+            thr_lo = thr_hi = us;
+          } else if (mode == 1) {
+            const float t = vhs_threshold_approx(us, a.vinv, a.lg2cv);
+            if (t > 0x1p-100f && t < 0x1p100f) {
+              thr_lo = fmul(t, kThrLo);
+              thr_hi = fmul(t, kThrHi);
+            } else {
+              thr_lo = thr_hi = vhs_threshold(us, a.vinv, a.lncv);
+            }
+          } else {
+            thr_lo = thr_hi = (us < a.cvhs) ? -1.0f : __int_as_float(0x7f800000);
+          }
           direction_of(w.z, w.w, nx, ny, nz);
         }
         // Earlier candidates of the batch that share a particle with this one: the
@@ -500,7 +568,9 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
             const float gx = fsub(ri.y, rj.y), gy = fsub(ri.z, rj.z), gz = fsub(ri.w, rj.w);
             const float g = fsqrt(fadd(fadd(fmul(gx, gx), fmul(gy, gy)), fmul(gz, gz)));
             gmax = fmaxf(gmax, g);
-            if (g > thr) {
+            bool accept = g > thr_hi;
+            if (!accept && g > thr_lo) accept = g > vhs_threshold(us, a.vinv, a.lncv);
+            if (accept) {
               const float hg = fmul(0.5f, g);
               const float cx = fmul(fadd(ri.y, rj.y), 0.5f);
               const float cy = fmul(fadd(ri.z, rj.z), 0.5f);
@@ -514,6 +584,8 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
           }
           __syncwarp();
         }
+        kb = first ? 31u : kb + 32u;
+        if (kb >= M) break;
       }
     }
     __syncwarp();
@@ -535,7 +607,7 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
         if (!hits) {
           const float xx = fadd(r.y, fmul(a.F, a.dt));
           P[gs + i] = make_float4(ynew, xx, r.z, r.w);
-          atomicAdd(&h[(gs + i >= mid ? n_cells : 0) + cell_of(ynew, n_cells, a.ncf)], 1);
+          count_cell(gs + i, cell_of(ynew, n_cells, a.ncf));
         }
       }
       const unsigned q = __ballot_sync(kFull, hits);
@@ -553,11 +625,13 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
                  a.open_top, a.u_top, a.p_top, inflow_fail))
           bad_bounce = true;
         P[p] = make_float4(yy, xx, uy, zz);
-        atomicAdd(&h[(p >= mid ? n_cells : 0) + cell_of(yy, n_cells, a.ncf)], 1);
+        count_cell(p, cell_of(yy, n_cells, a.ncf));
       }
     }
     __syncwarp();
     for (int i = lane; i < n_wall; i += 32) touch[i] = 0u;
+    // the records are read for the last time: bring in the next group's
+    if (q_next < n_groups) issue_copy(gs_next, gn_next);
     if (!add_group(m, sample, gn, nc, gmax, M, laccn, cfix + (size_t)lc * kNMom, &cgmax[lc],
                    &ccand[lc], &caccn[lc], lane))
       mom_range = true;
@@ -570,7 +644,7 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
   if (mom_range) atomicOr(err, kErrMoments);
   __syncthreads();
 
-  for (int i = threadIdx.x; i < R * n_cells; i += blockDim.x) row[i] = h[i];
+  write_rows();
   for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     const int lc = c - c0;
     const float gm = __uint_as_float(cgmax[lc]);

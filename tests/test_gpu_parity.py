@@ -157,7 +157,9 @@ def test_both_scatter_rankings_bitexact(case):
     dict(n_cells=64, ppc=250, Kn=1.0, collisions=False),  # sampling without collisions
     dict(n_cells=33, ppc=97, Kn=0.7, sample_start=7, dt_factor=0.5),
     dict(n_cells=16384, ppc=60, Kn=0.5, F=0.002),         # the largest cell count
-])
+    dict(n_cells=1, ppc=70000, Kn=0.5, omega=0.81),       # one cell of 274 groups
+    dict(n_cells=3, ppc=40000, Kn=2.0, span_particles=1 << 17, span_rows=2),  # a 120,000-
+])                                                        # particle span in two sort rows
 def test_edge_cases_deterministic(case):
     c = dict(case)
     o, g = make_pair(seed=11, **c)
