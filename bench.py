@@ -5,10 +5,19 @@ one JSON line on stdout.
 
 A step is one DSMC time step over every particle: collisions with the symmetric
 moment sample, free flight with the body force and the walls, and the stable cell
-sort (four kernel launches).  The line also carries, under "batched", the
-256-instance batched workload (one batch handle, tuned span partition, CUDA-graph
-replay) against the same instances stepped one after another as single runs.  The particle state (1.6 GB with its sort buffer) is
-resident in HBM and larger than L2, so no flush is needed between steps.
+sort (four kernel launches).  The particle state (1.6 GB with its sort buffer) is
+resident in HBM and larger than L2, so no flush is needed between steps.  Besides the
+headline, the line carries (one GPU):
+  precision   the same run with binary64 moment sums (options.accum) against the
+              default binary32 ones: time per step and their difference;
+  hs_kn1      the 20,000-particle hard-sphere run (L2-resident, launch-bound): time per
+              step under CUDA-graph replay;
+  batched     the 256-instance batched workload (one batch handle, tuned partition,
+              graph replay) against the same instances stepped as single runs;
+  serving     2,000 micro-solve requests arriving at 50/s, each to a 1 % standard
+              error of its channel-mean velocity, through the request loop
+              (continuous batching), against 8 of them solved one after another;
+  cpu_baseline / cpu_all_cores   the oracle on one and on all host cores.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
@@ -192,6 +201,38 @@ def cpu_baseline_sample(steps: int = 2) -> dict:
                       "single-threaded C oracle"}
 
 
+def _oracle_config0(seed: int) -> float:
+    """One full hard-sphere Kn = 1 run of the oracle (100 cells x 200 particles, 2,000
+    steps, the last 1,000 sampled); returns its seconds."""
+    import oracle
+    w = W.HS_KN1
+    s = oracle.OracleSim(omega=w.omega, Kn=w.Kn, F=w.body_force, n_cells=w.n_cells,
+                         ppc=w.ppc, seed=seed, sample_start=w.sample_start)
+    t0 = time.perf_counter()
+    s.step(w.steps)
+    t = time.perf_counter() - t0
+    s.close()
+    return t
+
+
+def cpu_all_cores() -> dict:
+    """The oracle on every host core at once: one process per core, each the full
+    hard-sphere Kn = 1 run with its own seed (processes started with spawn)."""
+    import multiprocessing as mp
+    P = os.cpu_count() or 1
+    w = W.HS_KN1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(P) as pool:
+        times = pool.map(_oracle_config0, range(100, 100 + P))
+    wall = time.perf_counter() - t0
+    work = P * w.n_particles * w.steps
+    return {"value": work / wall, "unit": METRIC, "cores": P, "kind": "oracle",
+            "sample": f"{P} processes, each the full {w.name} run ({w.steps} steps x "
+                      f"{w.n_particles} particles, own seed); wall {wall:.2f} s including "
+                      f"process start, slowest run {max(times):.2f} s",
+            "per_core_value": w.n_particles * w.steps / (sum(times) / len(times))}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -314,69 +355,157 @@ def run_batched(steps: int, warmup: int, rank: int) -> dict:
     }
 
 
-def run_serve(args, world, rank, local):
-    """Serving workload: Poisson arrivals of micro-solve requests drawn as the batched
-    workload, each run to a relative standard error of its channel-mean velocity, through
-    the library's request loop on one pool (continuous batching); beside it, the same
-    requests solved one at a time as plain runs (a sample of them)."""
+def run_precision(steps: int) -> dict:
+    """The benchmark workload with binary64 moment sums against the default binary32
+    ones: same seed, hence the same trajectory; `steps` sampled steps each, then the
+    time per step of each mode and the largest difference of the sums, relative to
+    count x <|v|^2>^(degree / 2) (the size of the sum of |products| up to a factor of
+    order one)."""
     import numpy as np
     import torch
-    from paper_2311_14140_gb300 import DsmcPool, _build, solve
-    _build.build()
-    torch.cuda.set_device(local)
-    reqs = W.serving_requests(args.requests, args.rate, args.target_se,
-                              seed=4242 + 1000 * rank)
+    from paper_2311_14140_gb300 import Dsmc
+    w = WORKLOAD
+    out, ms = {}, {}
+    for accum in (0, 1):
+        g = Dsmc(w.Kn, w.n_cells, w.ppc, omega=w.omega, body_force=w.body_force, seed=7,
+                 sample_start=1, group_size=w.group_size, dt_factor=w.dt_factor,
+                 accum=accum)
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[accum] = e0.elapsed_time(e1) / steps
+        out[accum] = g.moments()[0]
+        g.close()
+        torch.cuda.synchronize()
+    m32, m64 = out[0], out[1]
+    deg = np.array([0, 1, 1, 1, 2, 2, 2, 2, 2, 2, 3, 3, 3], np.float64)
+    cnt = np.maximum(m64[:, 0], 1.0)
+    e = np.maximum((m64[:, 4] + m64[:, 5] + m64[:, 6]) / cnt, 1e-30)
+    scale = cnt[:, None] * e[:, None] ** (deg / 2.0)
+    rel = np.abs(m32 - m64) / scale
+    return {"sampled_steps": steps,
+            "fp32": {"ms_per_step": ms[0], "accum": "binary32 per-lane sums (default)"},
+            "fp64": {"ms_per_step": ms[1], "accum": "binary64 per-lane sums"},
+            "fp32_vs_fp64_max_rel": float(rel.max()),
+            "fp32_vs_fp64_max_rel_by_degree": {str(d): float(rel[:, deg == d].max())
+                                               for d in (0, 1, 2, 3)}}
+
+
+def run_hs_kn1(steps: int = 2048) -> dict:
+    """The 20,000-particle hard-sphere Kn = 1 run (L2-resident, launch-bound): time per
+    step under CUDA-graph replay (16 steps per replay), sampling on."""
+    import torch
+    from paper_2311_14140_gb300 import Dsmc
+    w = W.HS_KN1
     side = torch.cuda.Stream()
-    clocks = Clocks(local)
     with torch.cuda.stream(side):
-        pool = DsmcPool(max_particles=args.pool_particles, max_cells=args.pool_particles // 50,
+        g = Dsmc(w.Kn, w.n_cells, w.ppc, omega=w.omega, body_force=w.body_force, seed=0,
+                 sample_start=1, graph=True, stream=side.cuda_stream)
+        g.step(64)
+        g.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        g.step(steps)
+        e1.record(side)
+        side.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        g.close()
+    return {"workload": w.name, "n_particles": w.n_particles, "steps": steps,
+            "us_per_step": 1e6 * t / steps, "value": w.n_particles * steps / t,
+            "unit": METRIC, "graph_replay": True,
+            "l2": "state 0.64 MB with its sort buffer: L2-resident, no HBM roofline"}
+
+
+def serve_leg(n_requests: int, rate: float, target_se: float, warmup_steps: int,
+              pool_particles: int, time_limit: float, sequential: int, rank: int) -> dict:
+    """Serving workload: Poisson arrivals of micro-solve requests drawn as the batched
+    workload, each run to a relative standard error of its channel-mean velocity
+    (capped at 200,000 steps), through the library's request loop on one pool
+    (continuous batching, graph replay); beside it, the first `sequential` requests
+    solved one after another as plain runs.  Micro-solves/s and latency percentiles
+    count requests that met their target only; capped and unfinished ones are reported
+    separately."""
+    import numpy as np
+    import torch
+    from paper_2311_14140_gb300 import DsmcPool, solve
+    reqs = W.serving_requests(n_requests, rate, target_se, seed=4242 + 1000 * rank)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        pool = DsmcPool(max_particles=pool_particles, max_cells=pool_particles // 50,
                         max_instances=4096, max_cells_per_instance=1000,
-                        sample_start=args.warmup_steps, graph=True, stream=side.cuda_stream)
-        barrier(world)
-        clocks.start()
+                        sample_start=warmup_steps, graph=True, stream=side.cuda_stream)
         t0 = time.perf_counter()
-        res = pool.serve(reqs, epoch_steps=32, batches=16)
+        res = pool.serve(reqs, epoch_steps=32, batches=16, time_limit=time_limit)
         wall = time.perf_counter() - t0
-        clk = clocks.stop()
         pool.close()
-    done = [r for r in res if r["finished"] >= 0 and r["converged"] >= 0]
-    lat = np.array([r["finished"] - q["arrival"] for r, q in zip(res, reqs)
-                    if r["finished"] >= 0 and r["converged"] >= 0])
+    conv = [k for k, r in enumerate(res) if r["converged"] == 1 and r["finished"] >= 0]
+    capped = sum(1 for r in res if r["converged"] == 0 and r["finished"] >= 0)
+    unfinished = sum(1 for r in res if r["finished"] < 0)
+    lat = np.array([res[k]["finished"] - reqs[k]["arrival"] for k in conv])
     qwait = np.array([r["admitted"] - q["arrival"] for r, q in zip(res, reqs)
                       if r["admitted"] >= 0])
     psteps = sum(r["steps"] * q["n_cells"] * q["ppc"] for r, q in zip(res, reqs))
-    # The same kind of requests one at a time as plain runs.
+    # The same requests one at a time as plain runs (graph replay on their own stream).
     seq = []
     t1 = time.perf_counter()
-    for q in reqs[:args.sequential_sample]:
-        seq.append(solve(q, epoch_steps=32, batches=16, sample_start=args.warmup_steps))
+    with torch.cuda.stream(side):
+        for q in reqs[:sequential]:
+            seq.append(solve(q, epoch_steps=32, batches=16, sample_start=warmup_steps,
+                             graph=True, stream=side.cuda_stream))
     t_seq = time.perf_counter() - t1
-    seq_psteps = sum(r["steps"] * q["n_cells"] * q["ppc"]
-                     for r, q in zip(seq, reqs[:args.sequential_sample]))
-    solves_per_s = len(done) / wall
-    line = {
-        "metric": "micro-solves/s", "value": world * solves_per_s, "unit": "micro-solves/s",
-        "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serving: Poisson arrivals, requests drawn as batch256",
-                   "requests": args.requests, "rate_per_s": args.rate,
-                   "target_se": args.target_se, "warmup_steps": args.warmup_steps,
-                   "pool_particles": args.pool_particles, "epoch_steps": 32,
-                   "se_batches": 16, "parallelism": f"replicas x{world}"},
-        "wall_s": wall, "finished": len(done),
-        "converged": sum(1 for r in res if r["converged"] == 1),
-        "latency_s": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
-                      "p99": float(np.percentile(lat, 99)) if lat.size else None,
-                      "max": float(lat.max()) if lat.size else None},
-        "queue_wait_s": {"p50": float(np.percentile(qwait, 50)) if qwait.size else None,
-                         "p99": float(np.percentile(qwait, 99)) if qwait.size else None},
+    seq_conv = sum(1 for r in seq if r["converged"] == 1)
+    seq_psteps = sum(r["steps"] * q["n_cells"] * q["ppc"] for r, q in zip(seq, reqs))
+
+    def pct(a, p):
+        return float(np.percentile(a, p)) if a.size else None
+
+    served = len(conv) / wall
+    seq_rate = seq_conv / t_seq if t_seq > 0 else None
+    return {
+        "metric": "micro-solves/s", "value": served, "unit": "micro-solves/s",
+        "workload": "serving: Poisson arrivals at 50/s, requests drawn as batch256 (Kn "
+                    "log-uniform [0.05, 10], 50-1000 cells, 50-400 ppc, force 0.5-2 x the "
+                    "Kn = 1 force), HS argon",
+        "requests": n_requests, "rate_per_s": rate, "target_se": target_se,
+        "max_steps": reqs[0]["max_steps"], "warmup_steps": warmup_steps,
+        "pool_particles": pool_particles, "epoch_steps": 32, "se_batches": 16,
+        "time_limit_s": time_limit, "wall_s": wall,
+        "converged": len(conv), "capped": capped, "unfinished": unfinished,
+        "latency_s_converged": {"p50": pct(lat, 50), "p99": pct(lat, 99),
+                                "max": float(lat.max()) if lat.size else None},
+        "queue_wait_s": {"p50": pct(qwait, 50), "p99": pct(qwait, 99)},
         "particle_steps_per_s": psteps / wall,
         "sequential_plain_solves": {
-            "requests": len(seq), "seconds": t_seq,
-            "solves_per_s": len(seq) / t_seq if t_seq > 0 else None,
+            "requests": len(seq), "converged": seq_conv, "seconds": t_seq,
+            "micro_solves_per_s": seq_rate,
             "particle_steps_per_s": seq_psteps / t_seq if t_seq > 0 else None},
-        "clocks": clk,
+        "served_over_sequential": (served / seq_rate) if seq_rate else None,
     }
+
+
+def run_serve(args, world, rank, local):
+    """The serving workload alone, as its own JSON line (all ranks serve their own
+    request streams: replicas)."""
+    import torch
+    from paper_2311_14140_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local)
+    barrier(world)
+    clocks = Clocks(local)
+    clocks.start()
+    leg = serve_leg(args.requests, args.rate, args.target_se, args.warmup_steps,
+                    args.pool_particles, args.serve_time_limit, args.sequential_sample, rank)
+    clk = clocks.stop()
+    line = dict(leg)
+    line.update({"value": world * leg["value"], "n_gpus": world, "higher_is_better": True,
+                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                 "config": {"workload": leg["workload"], "parallelism": f"replicas x{world}"},
+                 "clocks": clk})
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -419,21 +548,34 @@ def run_ours(args, world, rank, local):
     del g
     torch.cuda.synchronize()
 
-    # End-to-end region through the public API: create from parameters (device init),
-    # K steps each followed by a read of the moment sums into pinned host memory.
+    # End-to-end region through the public API, from host memory: the particle state
+    # (a checkpoint in pinned host memory) is loaded into a new run (host-to-device copy
+    # and sort into cells), then K steps, each followed by a read of the moment sums
+    # into pinned host memory.
+    g1 = Dsmc(w.Kn, w.n_cells, w.ppc, omega=w.omega, body_force=w.body_force,
+              seed=1000 + rank, sample_start=1, group_size=w.group_size,
+              dt_factor=w.dt_factor)
+    g1.step(2)
+    host = [torch.empty(N, dtype=torch.float32, pin_memory=True) for _ in range(4)]
+    g1.state_into(*host)
+    smax = g1.cells()[1]
+    g1.close()
+    del g1
     out = torch.empty((w.n_cells, 13), dtype=torch.float64, pin_memory=True)
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
     g2 = Dsmc(w.Kn, w.n_cells, w.ppc, omega=w.omega, body_force=w.body_force,
               seed=1000 + rank, sample_start=1, group_size=w.group_size,
               dt_factor=w.dt_factor)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g2.load_state(*host, smax=smax, step=2)
     for _ in range(args.steps):
         g2.step(1)
         g2.moments(out)
-    g2.close()
     torch.cuda.synchronize()
     t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    g2.close()
+    del g2, host
 
     value = world * N * args.steps / t_dev
     peak, peak_kind = peaks()
@@ -463,15 +605,33 @@ def run_ours(args, world, rank, local):
         "kernels": kernels,
         "clocks": clk,
         "e2e": {"value": world * N * args.steps / t_e2e, "unit": METRIC,
-                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": w.n_cells * 13 * 8,
-                "includes": "handle creation and device initialisation, K steps, a moment "
-                            "read into pinned host memory after every step"},
+                "h2d_bytes_per_step": 16 * N / args.steps,
+                "d2h_bytes_per_step": w.n_cells * 13 * 8,
+                "includes": "a host checkpoint of the state (16 B per particle, pinned) "
+                            "loaded into a run (copy and sort into cells; counted once and "
+                            "spread over the K steps), K steps, a moment read into pinned "
+                            "host memory after every step"},
         "gpu_launches": launches,
     }
+    def leg(name, fn):
+        try:
+            result[name] = fn()
+        except Exception as e:  # a failing extra leg must not lose the headline
+            result[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    if world == 1 and not args.no_extras:
+        leg("precision", lambda: run_precision(args.precision_steps))
+        leg("hs_kn1", run_hs_kn1)
     if not args.no_batched:
-        result["batched"] = run_batched(args.steps, args.warmup, rank)
+        leg("batched", lambda: run_batched(args.steps, args.warmup, rank))
+    if world == 1 and not args.no_serve:
+        leg("serving", lambda: serve_leg(args.requests, args.rate, args.target_se,
+                                         args.warmup_steps, args.pool_particles,
+                                         args.serve_time_limit, args.sequential_sample,
+                                         rank))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline_sample()
+        leg("cpu_all_cores", cpu_all_cores)
     if rank == 0:
         print(json.dumps(result), flush=True)
     return 0
@@ -487,10 +647,18 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 256-instance batched measurement")
     ap.add_argument("--serve", action="store_true",
-                    help="run the serving workload instead (its own JSON line)")
+                    help="run the serving workload alone (its own JSON line)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave the serving workload out of the main line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the precision and hard-sphere Kn = 1 measurements")
+    ap.add_argument("--precision-steps", type=int, default=1000)
+    ap.add_argument("--serve-time-limit", type=float, default=300.0,
+                    help="seconds after which the request loop stops (unfinished requests "
+                         "are reported as such)")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=50.0)
-    ap.add_argument("--target-se", type=float, default=0.05)
+    ap.add_argument("--target-se", type=float, default=0.01)
     ap.add_argument("--warmup-steps", type=int, default=256)
     ap.add_argument("--pool-particles", type=int, default=64_000_000)
     ap.add_argument("--sequential-sample", type=int, default=8)

@@ -665,12 +665,15 @@ def serve_options(**kw) -> ServeOptions:
     return so
 
 
-def solve(request: dict, *, epoch_steps: int = 32, batches: int = 16, **opts) -> dict:
-    """One request as a plain run of its own (``dsmc_solve``)."""
+def solve(request: dict, *, epoch_steps: int = 32, batches: int = 16, stream=None,
+          **opts) -> dict:
+    """One request as a plain run of its own (``dsmc_solve``) on ``stream`` (a
+    cudaStream_t as an integer; None: the legacy default stream)."""
     inst = {x: request[x] for x in request if x not in ("arrival", "target_se", "max_steps")}
     r = Request(make_instance(**inst), float(request.get("arrival", 0.0)),
                 float(request["target_se"]), int(request["max_steps"]))
     o = _options(**opts)
+    o.stream = int(stream) if stream is not None else None
     so = serve_options(epoch_steps=epoch_steps, batches=batches)
     res = RequestResult()
     _check(load_library().dsmc_solve(ctypes.byref(r), ctypes.byref(o), ctypes.byref(so),

@@ -145,3 +145,49 @@ def test_solve_alone_matches_serving_one_request():
     assert s["steps"] == r["steps"] and s["count"] == r["count"]
     # the same per-cell sums reduced over the instance's cells by the same kernel
     assert s["sum_vx"] == r["sum_vx"]
+
+
+def test_served_requests_and_pool_members_match_the_oracle():
+    """The oracle, not the library, as the reference of served work.  Three small requests
+    (hard spheres, VHS omega = 0.74, Kn 0.3-4) are served together; for each, the oracle
+    runs the same instance for the steps the loop reports: the sampled particle count
+    must agree exactly and the channel sum of vx within the DSMC parity bound
+    (2e-6 of the oracle's sum of |vx|).  A pool member that joins mid-run is also
+    compared with the oracle bit for bit (state, cell offsets, (sigma g)_max)."""
+    import oracle
+    from paper_2311_14140_gb300 import DsmcPool
+    defs = [dict(Kn=1.0, n_cells=30, ppc=50, omega=0.5, body_force=2e-3, seed=31),
+            dict(Kn=0.3, n_cells=24, ppc=80, omega=0.74, body_force=1e-3, seed=32),
+            dict(Kn=4.0, n_cells=40, ppc=30, omega=0.5, body_force=5e-3, seed=33)]
+    reqs = [dict(d, arrival=0.0, target_se=0.3, max_steps=320) for d in defs]
+    p = DsmcPool(max_particles=20_000, max_cells=400, max_instances=4,
+                 max_cells_per_instance=100, sample_start=8)
+    res = p.serve(reqs, epoch_steps=16, batches=4)
+    for r, d in zip(res, defs):
+        assert r["converged"] in (0, 1) and r["steps"] > 0
+        o = oracle.OracleSim(omega=d["omega"], Kn=d["Kn"], F=d["body_force"],
+                             n_cells=d["n_cells"], ppc=d["ppc"], seed=d["seed"],
+                             sample_start=8)
+        o.step(r["steps"])
+        m, _ = o.moments()
+        assert r["count"] == m[:, 0].sum()
+        assert abs(r["sum_vx"] - m[:, 1].sum()) <= 2e-6 * o.abs_moments()[:, 1].sum()
+        o.close()
+    # a member added to a running pool against the oracle
+    q = DsmcPool(max_particles=20_000, max_cells=400, max_instances=4,
+                 max_cells_per_instance=100, sample_start=3)
+    q.add(**defs[0])
+    q.step(5)
+    i = q.add(**defs[1])
+    q.step(11)
+    d = defs[1]
+    o = oracle.OracleSim(omega=d["omega"], Kn=d["Kn"], F=d["body_force"], n_cells=d["n_cells"],
+                         ppc=d["ppc"], seed=d["seed"], sample_start=3)
+    o.step(11)
+    for x, y in zip(o.state(), q.state(i)):
+        np.testing.assert_array_equal(x.view(np.uint32), y.view(np.uint32))
+    oo, so, _, _ = o.cells()
+    og, sg, _, _ = q.cells(i)
+    np.testing.assert_array_equal(oo, og)
+    np.testing.assert_array_equal(so.view(np.uint32), sg.view(np.uint32))
+    o.close()
