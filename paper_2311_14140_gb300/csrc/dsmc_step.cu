@@ -27,6 +27,8 @@
 //                    in flight, ranks each record among the same-cell records before it
 //                    and scatters it stably into the other buffer from the span's row of
 //                    the prefix-summed matrix plus the new cell offsets.
+//   k_scatter_coop   the same scatter with a CTA per span (up to 1,365 cells): all its
+//                    warps rank one round of 256 records at a time.
 //
 // Between them, k_scan_spans and k_offsets_cells (below) turn the matrix into per-span
 // bases and the new cell offsets.
@@ -828,6 +830,101 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
   if (bad) atomicOr(err, kErrSort);
 }
 
+// One CTA of kCoopWarps warps per (span, row): the stable scatter of the row's records
+// into the other buffer, kCoopWarps * 32 records per round.  In a round warp w takes the
+// 32 consecutive records [base + 32 w, base + 32 w + 32); a record's place is
+//   run[cell]                      the cell's next slot after the earlier rounds,
+// + sum over warps w' < w of       the round's records of w' bound for the same cell,
+// + its rank among the lanes of its own warp bound for the same cell (__match_any_sync).
+// Each warp publishes its per-cell counts in its own row of a table tagged with the
+// round number (no clearing between rounds); after the places are taken, every warp
+// adds its counts into run[].  All warps of the CTA work on one span at once: for
+// short spans of small instances (a batch) this beats a warp per span, whose time is
+// its span's ranking chain plus a pass over all of the instance's cells to set up run[].
+// Shared memory: run[n_cells] and the table kCoopWarps x n_cells, so it is used while
+// that leaves room for 4 CTAs per SM.
+constexpr int kCoopWarps = 8;
+constexpr size_t kCoopSmemMax = 48 * 1024;
+
+template <bool kBatch>
+__global__ void __launch_bounds__(kCoopWarps * 32)
+    k_scatter_coop(const float4* __restrict__ P, float4* __restrict__ P2,
+                   const int* __restrict__ off_cur_all, const int* __restrict__ off_new_all,
+                   const int* __restrict__ hist, const InstParams one, const StepLaunch SL,
+                   int* __restrict__ err) {
+  extern __shared__ int sh_coop[];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int R = SL.rows;
+  const int gspan = blockIdx.x / R, sub = blockIdx.x - gspan * R;
+  const InstParams& a = instance_of<kBatch>(one, SL, gspan);
+  const int n_cells = a.n_cells;
+  const int span = gspan - a.span_base;
+  const int* __restrict__ off_cur = off_cur_all + a.off_base;
+  const int* __restrict__ off_new = off_new_all + a.off_base;
+  int* run = sh_coop;
+  int* tab = sh_coop + n_cells;  // tab[w' * n_cells + c] = (round << 8) | count
+  const int* row = hist + a.hist_base + ((size_t)span * R + sub) * n_cells;
+  for (int c = threadIdx.x; c < n_cells; c += blockDim.x) run[c] = off_new[c] + row[c];
+  for (int i = threadIdx.x; i < kCoopWarps * n_cells; i += blockDim.x) tab[i] = -1;
+  const int c0 = span * a.cps;
+  const int c1 = min(c0 + a.cps, n_cells);
+  const int sb0 = off_cur[c0], sb1 = off_cur[c1];
+  const int mid = (R > 1) ? sb0 + ((sb1 - sb0) >> 1) : sb1;
+  const int b0 = (sub == 0) ? sb0 : mid;
+  const int b1 = (sub == 0) ? mid : sb1;
+  const int lo = a.part_base, hi = a.part_base + a.n_part;  // the instance's slots
+  const unsigned lt = (1u << lane) - 1u;
+  constexpr int kRound = kCoopWarps * 32;
+  constexpr int kAhead = 6;  // rounds of records in flight per lane
+  float4 r[kAhead];
+#pragma unroll
+  for (int u = 0; u < kAhead; ++u) {
+    const int p = b0 + u * kRound + w * 32 + lane;
+    if (p < b1) r[u] = P[p];
+  }
+  bool bad = false;
+  __syncthreads();
+  int round = 0;
+  for (int base = b0; base < b1; base += kAhead * kRound) {
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u, ++round) {
+      const int rb = base + u * kRound;
+      if (rb >= b1) break;  // uniform across the CTA
+      const int p = rb + w * 32 + lane;
+      const bool act = p < b1;
+      const float4 rec = r[u];
+      // the record kAhead rounds later into this register
+      const int pn = p + kAhead * kRound;
+      if (pn < b1) r[u] = P[pn];
+      const int cell = act ? cell_of(rec.x, n_cells, a.ncf) : -1;
+      const unsigned peers = __match_any_sync(kFull, cell);
+      const bool leader = act && (peers & lt) == 0u;
+      const int nw = __popc(peers);
+      if (leader) tab[w * n_cells + cell] = (round << 8) | nw;
+      __syncthreads();
+      if (act) {
+        int before = __popc(peers & lt);
+#pragma unroll
+        for (int v = 0; v < kCoopWarps - 1; ++v) {
+          if (v < w) {
+            const int e = tab[v * n_cells + cell];
+            if ((e >> 8) == round) before += e & 0xff;
+          }
+        }
+        const int d = run[cell] + before;
+        if (d >= lo && d < hi)
+          P2[d] = rec;
+        else
+          bad = true;
+      }
+      __syncthreads();
+      if (leader) atomicAdd(&run[cell], nw);
+    }
+  }
+  if (bad) atomicOr(err, kErrSort);
+}
+
 // Per instance and cell c: row r of the sort matrix <- sum over rows r' < r (the spans
 // before), count[c] <- total.  Block (32, 32): x = cell within a chunk of 32, y = one of
 // 32 contiguous row segments; grid (cell chunks, instances).
@@ -1049,9 +1146,24 @@ int scatter_spans_warps(int n_cells) {
   return w < 1 ? 1 : (int)w;
 }
 
+size_t scatter_coop_smem(int max_cells) {
+  return (size_t)(kCoopWarps + 1) * (size_t)max_cells * sizeof(int);
+}
+
 cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur,
                                  const int* off_new, const int* hist, const InstParams& one,
                                  const StepLaunch& L, int* err, cudaStream_t st) {
+  const size_t coop = scatter_coop_smem(L.max_cells);
+  if (coop <= kCoopSmemMax) {  // a CTA per (span, row)
+    const int units = L.n_spans_total * L.rows;
+    if (L.n_inst == 1)
+      k_scatter_coop<false><<<units, kCoopWarps * 32, coop, st>>>(P, P2, off_cur, off_new, hist,
+                                                                   one, L, err);
+    else
+      k_scatter_coop<true><<<units, kCoopWarps * 32, coop, st>>>(P, P2, off_cur, off_new, hist,
+                                                                  one, L, err);
+    return cudaGetLastError();
+  }
   const int wpb = scatter_spans_warps(L.max_cells);
   const size_t smem = (size_t)wpb * (L.max_cells + kMaskSlots) * sizeof(int);
   const int units = L.n_spans_total * L.rows;
@@ -1145,10 +1257,12 @@ cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes) {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a_bytes);
     if (e != cudaSuccess) return e;
   }
-  const void* scatter[4] = {(const void*)k_scatter_spans<false, false>,
+  const void* scatter[6] = {(const void*)k_scatter_spans<false, false>,
                             (const void*)k_scatter_spans<false, true>,
                             (const void*)k_scatter_spans<true, false>,
-                            (const void*)k_scatter_spans<true, true>};
+                            (const void*)k_scatter_spans<true, true>,
+                            (const void*)k_scatter_coop<false>,
+                            (const void*)k_scatter_coop<true>};
   for (const void* f : scatter) {
     const cudaError_t e =
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_bytes);

@@ -120,23 +120,30 @@ def test_vhs_kn01_multigroup_deterministic(warps, rows):
 
 
 @pytest.mark.parametrize("case", [
-    # particles crossing ~13 cells a step, 1,000 spans: the mask table
+    # up to 1,365 cells a CTA per span: 1,000 spans of one cell, particles crossing ~13
+    # cells a step
     dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=1024, spans=1000),
-    # the same run in 143 spans: __match_any_sync
-    dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=8192, spans=143),
-    # 1,000 spans of two sort rows each (a warp per row): the mask table on half-spans
+    # the same with two sort rows per span (a CTA per row)
     dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=1024, span_rows=2,
          spans=1000),
+    # more cells, a warp per span: 750 spans, the mask table
+    dict(Kn=0.1, omega=0.81, n_cells=1500, ppc=800, span_particles=1024, spans=750),
+    # the same run in 137 spans: __match_any_sync
+    dict(Kn=0.1, omega=0.81, n_cells=1500, ppc=800, span_particles=8192, spans=137),
+    # 750 spans of two sort rows each (a warp per row): the mask table on half-spans
+    dict(Kn=0.1, omega=0.81, n_cells=1500, ppc=800, span_particles=1024, span_rows=2,
+         spans=750),
     # Kn = 1 on 2,000 cells, particles crossing hundreds of cells a step, 1,000 spans:
     # the mask table with slices whose cells span 256 values or more (its fallback)
     dict(Kn=1.0, omega=0.5, n_cells=2000, ppc=600, span_particles=1024, spans=1000),
 ])
-def test_both_scatter_rankings_bitexact(case):
-    """The scatter ranks same-cell records with a shared-memory mask table when at least
-    four of its warps (spans) share an SM (a 152-SM GPU: 608 spans), else with
-    __match_any_sync; a slice whose cells span 256 values or more falls back to
-    __match_any_sync inside the mask-table kernel.  Each case bit-exact against the
-    oracle over 6 steps."""
+def test_scatter_variants_bitexact(case):
+    """The stable scatter runs a CTA per span while its shared memory (nine words per
+    cell) leaves room for 4 CTAs per SM (up to 1,365 cells); above, a warp per span,
+    which ranks same-cell records with a shared-memory mask table when at least four of
+    its warps (spans) share an SM (a 152-SM GPU: 608 spans), else with
+    __match_any_sync, and falls back to __match_any_sync for a slice whose cells span
+    256 values or more.  Each case bit-exact against the oracle over 6 steps."""
     c = dict(case)
     spans = c.pop("spans")
     o, g = make_pair(F=W.f0_force(c["Kn"]), seed=5, **c)
