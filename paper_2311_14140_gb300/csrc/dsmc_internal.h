@@ -18,7 +18,9 @@ constexpr int kMaxSpanRows = 2;    // rows of the sort matrix per span (halves o
 constexpr int kBWarpsMax = 4;      // warps (spans) per CTA of the span scatter
 constexpr int kMaxStepCells = 16384;
 constexpr int kMaxSpans = 152 * 16;   // rows of the per-step sort matrix, at most
-constexpr int kMaxCellsPerSpan = 256;
+// At most 24 cells per span: the CTA's per-cell slots stay small (at 4,096-particle spans
+// the batch of small instances keeps 5 CTAs per SM), 4 % faster than 256 on the batch.
+constexpr int kMaxCellsPerSpan = 24;
 constexpr size_t kStepSmemMax = 220 * 1024;
 constexpr int kSortWarpsMax = 152 * 16;
 constexpr int kSortWarpsPerBlock = 8;
