@@ -102,7 +102,7 @@ typedef struct dsmc_options {
   int profile;            /* 1: time every kernel launch with CUDA events (then
                              dsmc_step synchronises at its end); default 0 */
   int span_particles;     /* particles per span (CTA) of the step passes at the
-                             initial density: 0 keeps the partition in use (2048 at
+                             initial density: 0 keeps the partition in use (4096 at
                              creation, or what dsmc_autotune chose), else 1024..2^24.
                              Only the work split changes: results are identical for
                              every value; default 0 */

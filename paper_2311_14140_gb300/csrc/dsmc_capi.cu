@@ -53,7 +53,7 @@ const char* const kKernelNames[K_NUM] = {"init",          "collide_move", "scan_
                                          "cell_offsets",  "scatter_spans", "index_count",
                                          "index_scatter"};
 
-constexpr int kDefaultSpanParticles = 2048;
+constexpr int kDefaultSpanParticles = 4096;
 constexpr int kMinSpanParticles = 1024;
 constexpr int kMaxSpanParticles = 1 << 24;
 constexpr int kMaxInstances = 65535;  // grid y of the per-instance prefix pass
