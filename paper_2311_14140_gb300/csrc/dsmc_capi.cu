@@ -344,7 +344,7 @@ struct dsmc_sim {
   int span_target = kDefaultSpanParticles;
   int cta_warps = kAWarps;  // warps per CTA of the collide/move pass
   int span_rows = 1;        // sort-matrix rows per span
-  int spans = 0, max_cps = 1, max_cells = 1;  // partition in use
+  int spans = 0, max_cps = 1, max_cells = 1, max_spans = 1;  // partition in use
   int spans_reserved = 0;
   Capacity C{};
   Layout L{};
@@ -456,7 +456,7 @@ void partition_extent(const dsmc_sim* h, int target, const Inst* extra, int* max
 void set_partition(dsmc_sim* h, int target) {
   h->span_target = target;
   h->span_inst.clear();
-  int base = 0, m = 1, mc = 1;
+  int base = 0, m = 1, mc = 1, ms = 1;
   for (int t = 0; t < h->n_inst(); ++t) {
     Inst& x = h->inst[h->order[t]];
     make_spans(x.n_cells, x.ppc, target, &x.cps, &x.n_spans);
@@ -464,11 +464,13 @@ void set_partition(dsmc_sim* h, int target) {
     base += x.n_spans;
     m = std::max(m, x.cps);
     mc = std::max(mc, x.n_cells);
+    ms = std::max(ms, x.n_spans);
     h->span_inst.insert(h->span_inst.end(), (size_t)x.n_spans, t);
   }
   h->spans = base;
   h->max_cps = m;
   h->max_cells = mc;
+  h->max_spans = ms;
   h->tab_dirty = h->spans_dirty = true;
   h->graph_valid = false;
 }
@@ -547,6 +549,7 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   L.span_inst = h->span_inst_dev;
   L.n_spans_total = h->spans;
   L.max_cells = h->max_cells;
+  L.max_spans = h->max_spans;
   L.max_cps = h->max_cps;
   L.max_cap = h->cap();
   L.warps = h->cta_warps;
@@ -618,7 +621,7 @@ dsmc_status admit_fresh(dsmc_sim* h) {
   const int idle = h->cur ^ 1, oidle = h->ocur ^ 1;
   h->adm_tab.clear();
   h->adm_span.clear();
-  int base = 0, m = 1, mc = 1;
+  int base = 0, m = 1, mc = 1, ms = 1;
   for (size_t k = 0; k < ids.size(); ++k) {
     const Inst& x = h->inst[ids[k]];
     h->adm_tab.push_back(instance_params(h, ids[k], base));
@@ -626,6 +629,7 @@ dsmc_status admit_fresh(dsmc_sim* h) {
     base += x.n_spans;
     m = std::max(m, x.cps);
     mc = std::max(mc, x.n_cells);
+    ms = std::max(ms, x.n_spans);
     DSMC_CUDA(timed(h, K_INIT, [&] {
                 return launch_init(h->P[idle] + x.part_base, (int)x.N, x.ppc, (float)x.n_cells,
                                    (uint32_t)(x.seed & 0xffffffffu), (uint32_t)(x.seed >> 32),
@@ -650,6 +654,7 @@ dsmc_status admit_fresh(dsmc_sim* h) {
   SL.span_inst = adm_span_dev;
   SL.n_spans_total = base;
   SL.max_cells = mc;
+  SL.max_spans = ms;
   SL.max_cps = m;
   SL.max_cap = h->cap();
   SL.warps = h->cta_warps;

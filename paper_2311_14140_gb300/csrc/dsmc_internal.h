@@ -15,7 +15,10 @@ constexpr int kMaxGroup = 512;     // largest collision group size G
 constexpr int kAWarps = 8;         // warps per CTA of the collide/move pass (default)
 constexpr int kAWarpsSmall = 4;    // the other CTA shape the tuner may choose
 constexpr int kMaxSpanRows = 2;    // rows of the sort matrix per span (halves of its slots)
-constexpr int kBWarpsMax = 4;      // warps (spans) per CTA of the span scatter
+// Warps (spans) per CTA of the span scatter.  Small CTAs spread the spans evenly over the
+// SMs: 2,000 one-warp spans as 4-warp CTAs leave 44 SMs with 16 warps and the rest with
+// 12, and the SMs with 16 set the kernel's time (0.355 ms against 0.339 ms with 2-warp CTAs).
+constexpr int kBWarpsMax = 2;
 constexpr int kMaxStepCells = 16384;
 constexpr int kMaxSpans = 152 * 16;   // rows of the per-step sort matrix, at most
 // At most 24 cells per span: the CTA's per-cell slots stay small (at 4,096-particle spans
@@ -177,6 +180,7 @@ struct StepLaunch {
   const int* span_inst;   // device, one entry per global span (batched launches)
   int n_spans_total;
   int max_cells;         // largest n_cells of the instances
+  int max_spans;         // largest n_spans of the instances
   int max_cps;
   int max_cap;
   int warps;             // warps per CTA of the collide/move pass (kAWarps or kAWarpsSmall)

@@ -4,8 +4,9 @@ An instance of a batch draws its random numbers from its own seed, step, cells a
 slots, so it must evolve bit for bit as the same run on its own, and hence as the
 oracle.  The span partition of the step passes, the tuner and CUDA-graph replay change
 only how work is split and launched, so none of them may change a single bit either.
-Moment sums are compared within the tolerance of the parity tests (the order of the
-binary64 atomic additions varies between launches).
+Moment sums of two CUDA runs are compared bit for bit (group totals combine exactly in
+fixed point, whatever the order); against the oracle's binary64 sums, within the
+tolerance of the parity tests.
 """
 import numpy as np
 import pytest
@@ -127,6 +128,21 @@ def test_partition_does_not_change_results(span, warps, rows):
     b.step(3)
     for i in range(len(DEFS)):
         assert_same_run(Member(ref, i), Member(b, i))
+
+
+def test_batch_with_a_member_of_many_spans():
+    """A member of 300 one-cell spans makes the batch's sort matrix too tall for the
+    column-walk prefix (more than 256 rows): the batch takes the segmented prefix kernel,
+    its members alone take either; every member still matches its run alone."""
+    defs = [dict(Kn=1.0, n_cells=300, ppc=1100, omega=0.5, body_force=W.f0_force(1.0),
+                 seed=8), DEFS[1], DEFS[2]]
+    b = batch(defs, span_particles=1024, sample_start=2)
+    b.step(6)
+    assert b.info(0)["n_spans"] == 300
+    for i, d in enumerate(defs):
+        s = single(d, span_particles=1024, sample_start=2)
+        s.step(6)
+        assert_same_run(s, Member(b, i))
 
 
 def test_autotune_keeps_the_run():

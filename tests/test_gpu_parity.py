@@ -153,6 +153,23 @@ def test_scatter_variants_bitexact(case):
     assert_bitexact(o, g)
 
 
+@pytest.mark.parametrize("n_cells,rows,kernel", [
+    (256, 1, "cols"), (257, 1, "spans"), (128, 2, "cols"), (129, 2, "spans")])
+def test_span_prefix_kernels_bitexact(n_cells, rows, kernel):
+    """The prefix of the sort matrix down its rows runs as one thread per cell walking
+    its column while an instance has at most 256 rows (spans x sort rows), else as blocks
+    of 32 cells x 32 row segments.  One-cell spans put each case on either side of the
+    threshold; every case bit-exact against the oracle over 5 steps."""
+    o, g = make_pair(Kn=1.0, n_cells=n_cells, ppc=1100, F=W.f0_force(1.0), seed=21,
+                     span_particles=1024, span_rows=rows)
+    info = g.info()
+    assert info["n_spans"] == n_cells and info["cells_per_span"] == 1
+    assert (n_cells * rows <= 256) == (kernel == "cols")
+    o.step(5)
+    g.step(5)
+    assert_bitexact(o, g)
+
+
 @pytest.mark.parametrize("case", [
     dict(n_cells=1, ppc=2, Kn=1.0),                       # one cell, smallest pair
     dict(n_cells=37, ppc=13, Kn=0.5, F=0.01),             # N = 481, ragged warp tail
