@@ -235,8 +235,8 @@ int reserved_spans(int n_cells, int ppc) {
 }
 
 // Workspace layout for a capacity: two record buffers, the sort matrix, per-cell
-// arrays, two instance tables and two span tables (the step's and the admission
-// pass's), the channel sums and the error word.
+// arrays, two instance tables, two span tables (the step's and the admission pass's)
+// and the step's span order, the channel sums and the error word.
 Layout layout_of(const Capacity& C) {
   Layout L{};
   size_t o = 0;
@@ -261,7 +261,7 @@ Layout layout_of(const Capacity& C) {
   L.tab = o;
   o += align256(2 * (size_t)C.inst * sizeof(InstParams));
   L.span_inst = o;
-  o += align256(2 * (size_t)C.spans * sizeof(int));
+  o += align256(3 * (size_t)C.spans * sizeof(int));
   L.chan = o;
   o += align256(2 * (size_t)C.inst * sizeof(double));
   L.err = o;
@@ -362,10 +362,11 @@ struct dsmc_sim {
   double* acc = nullptr;
   double* fields = nullptr;  // dsmc_cell_fields_of's output on the device
   InstParams* tab_dev = nullptr;  // [0, C.inst): the step's; [C.inst, 2 C.inst): admission
-  int* span_inst_dev = nullptr;   // likewise with C.spans entries each
+  int* span_inst_dev = nullptr;   // likewise with C.spans entries each, then the order
+  int* span_order_dev = nullptr;  // the span each collide/move CTA takes (C.spans entries)
   double* chan_dev = nullptr;
   std::vector<InstParams> tab, adm_tab;
-  std::vector<int> span_inst, adm_span;
+  std::vector<int> span_inst, adm_span, span_order;
   bool tab_dirty = true, spans_dirty = true;
   // CUDA graph of kGraphSteps consecutive steps, replayed by dsmc_step when
   // options.graph is set.  Its kernels read the global step from gstep_dev, which the
@@ -452,6 +453,37 @@ void partition_extent(const dsmc_sim* h, int target, const Inst* extra, int* max
   *max_cells = mc;
 }
 
+// Launch order of the collide/move CTAs: the spans by estimated cost, heaviest first, so
+// that the pass does not end on a few slow CTAs started last (the spans at the top wall of
+// a run started in cell order ran about twice as long as the rest and left most SMs idle
+// for the last sixth of the pass).  A span's cost is taken as its particles times
+// (1 + 2.2 h), h the expected wall hits per particle and step: with normal velocity
+// components of variance 1/2 (v0 units), a particle at distance d from a wall reaches it
+// within dt with probability erfc(d / dt) / 2, evaluated at the span's centre for both
+// walls; 2.2 is the measured extra cost of a hit relative to a particle's other work in the
+// step (a batch at Kn = 10, about one hit per particle and step, costs 3.2 times one at
+// Kn = 0.1).  The order changes which CTA takes a span, never a result.
+void set_span_order(dsmc_sim* h) {
+  std::vector<std::pair<double, int>> cost;
+  cost.reserve((size_t)h->spans);
+  for (int t = 0; t < h->n_inst(); ++t) {
+    const Inst& x = h->inst[h->order[t]];
+    const double dt = x.p.dt;
+    for (int k = 0; k < x.n_spans; ++k) {
+      const int c0 = k * x.cps, c1 = std::min(c0 + x.cps, x.n_cells);
+      const double yc = 0.5 * (c0 + c1) / x.n_cells;
+      const double hits = dt > 0.0 ? 0.5 * (std::erfc(yc / dt) + std::erfc((1.0 - yc) / dt)) : 0.0;
+      cost.emplace_back(-(double)(c1 - c0) * x.ppc * (1.0 + 2.2 * hits), x.span_base + k);
+    }
+  }
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+                     return a.first < b.first;
+                   });
+  h->span_order.resize(cost.size());
+  for (size_t i = 0; i < cost.size(); ++i) h->span_order[i] = cost[i].second;
+}
+
 // Assigns spans with `target` particles per span to every active instance.
 void set_partition(dsmc_sim* h, int target) {
   h->span_target = target;
@@ -471,6 +503,7 @@ void set_partition(dsmc_sim* h, int target) {
   h->max_cps = m;
   h->max_cells = mc;
   h->max_spans = ms;
+  set_span_order(h);
   h->tab_dirty = h->spans_dirty = true;
   h->graph_valid = false;
 }
@@ -537,6 +570,11 @@ dsmc_status upload_tables(dsmc_sim* h) {
                                 h->span_inst.size() * sizeof(int), cudaMemcpyHostToDevice,
                                 h->stream()),
                 "span table");
+    if (!h->span_order.empty())
+      DSMC_CUDA(cudaMemcpyAsync(h->span_order_dev, h->span_order.data(),
+                                h->span_order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                h->stream()),
+                "span order");
     h->spans_dirty = false;
   }
   return DSMC_OK;
@@ -547,6 +585,7 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   L.n_inst = h->n_inst();
   L.tab = h->tab_dev;
   L.span_inst = h->span_inst_dev;
+  L.span_order = h->span_order.empty() ? nullptr : h->span_order_dev;
   L.n_spans_total = h->spans;
   L.max_cells = h->max_cells;
   L.max_spans = h->max_spans;
@@ -911,6 +950,7 @@ dsmc_status new_handle(const Capacity& C, const dsmc_options& opt, bool pool, vo
   h->fields = (double*)(b + L.fields);
   h->tab_dev = (InstParams*)(b + L.tab);
   h->span_inst_dev = (int*)(b + L.span_inst);
+  h->span_order_dev = h->span_inst_dev + 2 * (size_t)h->C.spans;
   h->chan_dev = (double*)(b + L.chan);
   h->err = (int*)(b + L.err);
   h->gstep_dev = (long long*)(b + L.err + 8);

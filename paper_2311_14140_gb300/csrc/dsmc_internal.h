@@ -178,6 +178,7 @@ struct StepLaunch {
   int n_inst;
   const InstParams* tab;  // device, n_inst entries (batched launches)
   const int* span_inst;   // device, one entry per global span (batched launches)
+  const int* span_order;  // device or NULL: collide/move CTA b takes span span_order[b]
   int n_spans_total;
   int max_cells;         // largest n_cells of the instances
   int max_spans;         // largest n_spans of the instances

@@ -5,7 +5,8 @@
 // 16-byte load or store moves a whole particle, so the sort's scattered writes cost
 // one L2 sector per particle instead of four.
 //
-//   k_collide_move   one CTA per span of consecutive cells.  Its warps take the span's
+//   k_collide_move   one CTA per span of consecutive cells, the heaviest spans launched
+//                    first (an order the host estimates).  Its warps take the span's
 //                    collision groups one after another (a shared counter hands them
 //                    out) and for each group
 //                      1. load the group's records, keep them in shared memory and add
@@ -313,7 +314,9 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
   // unrolling the per-particle loops helps the single run; the batched kernel, which
   // already spills, was 16 % slower with it
   constexpr int kMoveUnroll = kBatch ? 1 : 4;
-  const InstParams& a = stage_instance<kBatch>(one, SL, blockIdx.x, &sh_inst);
+  // the global span of this CTA: the launch takes spans heaviest first
+  const int gspan = SL.span_order ? SL.span_order[blockIdx.x] : (int)blockIdx.x;
+  const InstParams& a = stage_instance<kBatch>(one, SL, gspan, &sh_inst);
   const int* __restrict__ off = off_all + a.off_base;
   const float* __restrict__ smax_in = smax_in_all + a.cell_base;
   float* __restrict__ smax_out = smax_out_all + a.cell_base;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(kWarps * 32, (collide_ctas_per_sm<kBatch, kWar
   unsigned* touch = reinterpret_cast<unsigned*>(wmem + L.w_own);
   uint64_t* bar = reinterpret_cast<uint64_t*>(wmem + L.w_bar);
 
-  const int span = blockIdx.x - a.span_base;  // the instance's span
+  const int span = gspan - a.span_base;  // the instance's span
   const int c0 = span * cps;
   const int c1 = min(c0 + cps, n_cells);
   const unsigned lt = (1u << lane) - 1u;
