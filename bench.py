@@ -279,11 +279,13 @@ def batch_defs(n: int = 256):
                  body_force=w.body_force, seed=w.seeds[0]) for w in W.batch_instances(n)]
 
 
-def run_batched(steps: int, warmup: int, rank: int) -> dict:
+def run_batched(steps: int, warmup: int, rank: int, span: int = 0,
+                sequential: bool = True) -> dict:
     """The 256-instance batched workload (Kn log-uniform in [0.05, 10], 50-1000 cells,
     50-400 particles per cell, force 0.5-2 x the Kn = 1 force): one batch handle with
-    the tuned span partition, steps replayed as CUDA graphs, against the same instances
-    stepped one after another as plain single runs."""
+    the tuned span partition (or `span` particles per span on 4-warp CTAs), steps
+    replayed as CUDA graphs, against the same instances stepped one after another as
+    plain single runs (unless `sequential` is false)."""
     import torch
     from paper_2311_14140_gb300 import Dsmc, DsmcBatch
     defs = batch_defs()
@@ -293,8 +295,13 @@ def run_batched(steps: int, warmup: int, rank: int) -> dict:
     n_part = sum(d["n_cells"] * d["ppc"] for d in defs)
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
-        b = DsmcBatch(defs, sample_start=1, graph=True, stream=side.cuda_stream)
-        best, tuned_ms = b.autotune(steps_per_trial=3)
+        if span:
+            b = DsmcBatch(defs, sample_start=1, graph=True, stream=side.cuda_stream,
+                          span_particles=span, cta_warps=4)
+            best = span
+        else:
+            b = DsmcBatch(defs, sample_start=1, graph=True, stream=side.cuda_stream)
+            best, tuned_ms = b.autotune(steps_per_trial=3)
         b.step(max(warmup, 16))
         b.sync()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -313,6 +320,25 @@ def run_batched(steps: int, warmup: int, rank: int) -> dict:
         b.close()
         del b
     torch.cuda.synchronize()
+    ms_cm, n_cm = kt.get("collide_move", (0.0, 0))
+    tot = sum(v[0] for v in kt.values())
+    peak, peak_kind = peaks()
+    value = n_part * steps / t_batch
+    out = {
+        "workload": "batch256: Kn log-uniform [0.05,10], 50-1000 cells, 50-400 ppc, HS argon",
+        "n_instances": len(defs), "n_particles": n_part, "steps": steps,
+        "value": value, "unit": METRIC, "ms_per_step": 1e3 * t_batch / steps,
+        "instance_steps_per_s": len(defs) * steps / t_batch,
+        "span_particles": best, "graph_replay": True,
+        "effective_step": {"bytes_per_particle_step": 32,
+                           "gbs": 32.0 * value / 1e9, "frac": 32.0 * value / 1e9 / peak,
+                           "peak_kind": peak_kind},
+        "collide_move_share": ms_cm / tot if tot else None,
+        "collide_move_gbs": (32.0 * n_part / (ms_cm / 1e3 / n_cm) / 1e9) if n_cm else None,
+        "cells_per_span_instance0": info["cells_per_span"],
+    }
+    if not sequential:
+        return out
     # The same instances as separate plain runs, stepped one after another.
     runs = [Dsmc(sample_start=1, **d) for d in defs]
     stream = torch.cuda.current_stream()
@@ -332,27 +358,11 @@ def run_batched(steps: int, warmup: int, rank: int) -> dict:
         r.close()
     del runs
     torch.cuda.synchronize()
-    ms_cm, n_cm = kt.get("collide_move", (0.0, 0))
-    tot = sum(v[0] for v in kt.values())
-    peak, peak_kind = peaks()
-    value = n_part * steps / t_batch
-    return {
-        "workload": "batch256: Kn log-uniform [0.05,10], 50-1000 cells, 50-400 ppc, HS argon",
-        "n_instances": len(defs), "n_particles": n_part, "steps": steps,
-        "value": value, "unit": METRIC, "ms_per_step": 1e3 * t_batch / steps,
-        "instance_steps_per_s": len(defs) * steps / t_batch,
-        "span_particles": best, "graph_replay": True,
-        "effective_step": {"bytes_per_particle_step": 32,
-                           "gbs": 32.0 * value / 1e9, "frac": 32.0 * value / 1e9 / peak,
-                           "peak_kind": peak_kind},
-        "collide_move_share": ms_cm / tot if tot else None,
-        "collide_move_gbs": (32.0 * n_part / (ms_cm / 1e3 / n_cm) / 1e9) if n_cm else None,
-        "sequential_single_runs": {"value": n_part * seq_steps / t_seq, "unit": METRIC,
-                                   "ms_per_step": 1e3 * t_seq / seq_steps,
-                                   "steps": seq_steps},
-        "speedup_vs_sequential": (n_part * steps / t_batch) / (n_part * seq_steps / t_seq),
-        "cells_per_span_instance0": info["cells_per_span"],
-    }
+    out["sequential_single_runs"] = {"value": n_part * seq_steps / t_seq, "unit": METRIC,
+                                     "ms_per_step": 1e3 * t_seq / seq_steps,
+                                     "steps": seq_steps}
+    out["speedup_vs_sequential"] = value / (n_part * seq_steps / t_seq)
+    return out
 
 
 def run_precision(steps: int) -> dict:
@@ -511,6 +521,30 @@ def run_serve(args, world, rank, local):
     return 0
 
 
+def run_batched_only(args, world, rank, local):
+    """The batched workload alone, as its own JSON line: a fixed partition when
+    --batch-span is given (no tuning, no sequential comparison: a profiling case)."""
+    import torch
+    from paper_2311_14140_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(local)
+    barrier(world)
+    clocks = Clocks(local)
+    clocks.start()
+    leg = run_batched(args.steps, args.warmup, rank, span=args.batch_span,
+                      sequential=not args.batch_span)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": leg["workload"], "parallelism": f"replicas x{world}"},
+            "value": world * leg["value"], "ms_per_step": leg["ms_per_step"],
+            "batched": leg, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -662,6 +696,11 @@ def main():
     ap.add_argument("--warmup-steps", type=int, default=256)
     ap.add_argument("--pool-particles", type=int, default=64_000_000)
     ap.add_argument("--sequential-sample", type=int, default=8)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run the 256-instance batched workload alone (its own JSON line)")
+    ap.add_argument("--batch-span", type=int, default=0,
+                    help="with --batched-only: particles per span instead of tuning, and "
+                         "no sequential comparison (profiling cases)")
     ap.add_argument("--cells", type=int, default=None,
                     help="override the cell count (profiling cases only)")
     ap.add_argument("--ppc", type=int, default=None,
@@ -678,6 +717,8 @@ def main():
             return run_reference(args, world, rank)
         if args.serve:
             return run_serve(args, world, rank, local)
+        if args.batched_only:
+            return run_batched_only(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:
