@@ -102,8 +102,10 @@ typedef struct dsmc_options {
   int profile;            /* 1: time every kernel launch with CUDA events (then
                              dsmc_step synchronises at its end); default 0 */
   int span_particles;     /* particles per span (CTA) of the step passes at the
-                             initial density: 0 keeps the partition in use (4096 at
-                             creation, or what dsmc_autotune chose), else 1024..2^24.
+                             initial density: 0 keeps the partition in use (at creation
+                             4096, or fewer down to 1024 when the handle holds less than
+                             two such spans per SM; or what dsmc_autotune chose), else
+                             1024..2^24.
                              Only the work split changes: results are identical for
                              every value; default 0 */
   int cta_warps;          /* warps per CTA of the collide/move pass: 0 keeps the shape

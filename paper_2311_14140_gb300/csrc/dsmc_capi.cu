@@ -894,6 +894,21 @@ dsmc_status add_instance(dsmc_sim* h, const dsmc_instance& d, int index, int n_d
   return DSMC_OK;
 }
 
+// Default particles per span for a handle of n particles: 4,096, or fewer for a small run
+// so that its step passes still spread over two CTAs per SM (a 20,000-particle run: 17
+// spans of 1,024 particles instead of 5 of 4,096), never below the finest partition its
+// sort matrix is sized for.
+int default_span_particles(long long n) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    sms = 152;
+  const long long t = n / (2LL * sms);
+  return (int)std::max<long long>(kMinSpanParticles,
+                                  std::min<long long>(kDefaultSpanParticles, t));
+}
+
 // Allocates the handle and its device workspace for capacity C.
 dsmc_status new_handle(const Capacity& C, const dsmc_options& opt, bool pool, void* workspace,
                        size_t workspace_bytes, dsmc_sim** out) {
@@ -903,7 +918,7 @@ dsmc_status new_handle(const Capacity& C, const dsmc_options& opt, bool pool, vo
   h->opt = opt;
   h->C = C;
   h->L = layout_of(C);
-  h->span_target = opt.span_particles ? opt.span_particles : kDefaultSpanParticles;
+  h->span_target = opt.span_particles ? opt.span_particles : default_span_particles(C.slots);
   // A pool holds many small instances whose membership changes too often to tune live;
   // 4-warp CTAs are what dsmc_autotune picks for such batches (8 % more micro-solves/s
   // than 8-warp CTAs in the request loop).
