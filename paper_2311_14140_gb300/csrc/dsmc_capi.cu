@@ -614,11 +614,16 @@ dsmc_status launch_pass(dsmc_sim* h, bool count_only, const StepLaunch& SL,
                                          h->hist, one, SL, h->err, s);
             }),
             count_only ? "index_count" : "collide_move");
-  DSMC_CUDA(timed(h, K_SCAN, [&] { return launch_scan_spans(h->hist, h->count, one, SL, s); }),
-            "scan_hist");
-  DSMC_CUDA(timed(h, K_OFFSETS,
-                  [&] { return launch_offsets_cells(h->count, off_new, one, SL, s); }),
-            "cell_offsets");
+  if (prefix_small_fits(SL)) {  // both prefix passes in one launch (timed as the scan)
+    DSMC_CUDA(timed(h, K_SCAN, [&] { return launch_prefix_small(h->hist, off_new, one, SL, s); }),
+              "prefix");
+  } else {
+    DSMC_CUDA(timed(h, K_SCAN, [&] { return launch_scan_spans(h->hist, h->count, one, SL, s); }),
+              "scan_hist");
+    DSMC_CUDA(timed(h, K_OFFSETS,
+                    [&] { return launch_offsets_cells(h->count, off_new, one, SL, s); }),
+              "cell_offsets");
+  }
   DSMC_CUDA(timed(h, count_only ? K_INDEX_SCATTER : K_SCATTER_SPANS, [&] {
               return launch_scatter_spans(h->P[src], h->P[src ^ 1], off_cur, off_new, h->hist,
                                           one, SL, h->err, s);

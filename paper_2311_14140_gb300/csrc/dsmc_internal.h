@@ -208,6 +208,11 @@ cudaError_t launch_scan_spans(int* hist, int* count, const InstParams& one, cons
                               cudaStream_t st);
 cudaError_t launch_offsets_cells(const int* count, int* off_new, const InstParams& one,
                                  const StepLaunch& L, cudaStream_t st);
+// Both prefix passes as one launch, when prefix_small_fits(L) (one instance, few cells
+// and rows).
+bool prefix_small_fits(const StepLaunch& L);
+cudaError_t launch_prefix_small(int* hist, int* off_new, const InstParams& one,
+                                const StepLaunch& L, cudaStream_t st);
 cudaError_t launch_set_counter(long long* counter, long long value, cudaStream_t st);
 // Per-cell arrays of newly added instances (table `tab`, n of them): moment sums and
 // collision counters zeroed, (sigma g)_max set to smax0, and cell offsets of whole

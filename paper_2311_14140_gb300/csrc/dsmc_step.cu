@@ -1064,6 +1064,76 @@ __global__ void __launch_bounds__(1024)
   if (SL.gstep_dev != nullptr && blockIdx.x == 0 && t == 0) *SL.gstep_dev += 1;
 }
 
+// Both prefix passes in one launch for a single instance of at most kPrefixSmallCells
+// cells and kScanColsMaxRows sort rows (a small run, whose step is launch-bound): one
+// CTA, thread c walks cell c's column of the matrix (its exclusive prefix over the spans,
+// 8 rows of loads in flight), then the CTA scans the cells' totals into the new offsets.
+// (For a batch, a CTA per instance this way was slower than the two launches.)
+constexpr int kPrefixSmallCells = 1024;
+
+__global__ void __launch_bounds__(kPrefixSmallCells, 2)
+    k_prefix_small(int* __restrict__ hist, int* __restrict__ off_new_all, const InstParams a,
+                   const StepLaunch SL) {
+  __shared__ int wsum[kPrefixSmallCells / 32];
+  const int n_cells = a.n_cells;
+  const int c = threadIdx.x;
+  const int n_rows = a.n_spans * SL.rows;
+  int run = 0;  // cell c's particles over all rows
+  if (c < n_cells) {
+    int* __restrict__ m = hist + a.hist_base + c;  // m[r n_cells]: row r of this column
+    for (int r = 0; r < n_rows; r += 8) {
+      int v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (r + u < n_rows) v[u] = m[(size_t)(r + u) * n_cells];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (r + u < n_rows) {
+          m[(size_t)(r + u) * n_cells] = run;
+          run += v[u];
+        }
+    }
+  }
+  // exclusive prefix of the totals over the cells: within each warp, then over warps
+  const int lane = c & 31, w = c >> 5;
+  int incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int x = wsum[lane];
+    int y = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, y, o);
+      if (lane >= o) y += t;
+    }
+    wsum[lane] = y - x;
+  }
+  __syncthreads();
+  const int excl = wsum[w] + incl - run;
+  int* __restrict__ offset = off_new_all + a.off_base;
+  if (c < n_cells) offset[c] = a.part_base + excl;
+  if (c == n_cells - 1) offset[n_cells] = a.part_base + excl + run;
+  // Graph replay: the step's collide/move pass has finished reading the step number.
+  if (SL.gstep_dev != nullptr && c == 0) *SL.gstep_dev += 1;
+}
+
+bool prefix_small_fits(const StepLaunch& L) {
+  return L.n_inst == 1 && L.max_cells <= kPrefixSmallCells &&
+         (long long)L.max_spans * L.rows <= kScanColsMaxRows;
+}
+
+cudaError_t launch_prefix_small(int* hist, int* off_new, const InstParams& one,
+                                const StepLaunch& L, cudaStream_t st) {
+  k_prefix_small<<<1, kPrefixSmallCells, 0, st>>>(hist, off_new, one, L);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_counter(long long* counter, long long value) { *counter = value; }
 
 __global__ void __launch_bounds__(256)

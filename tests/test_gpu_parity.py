@@ -153,18 +153,22 @@ def test_scatter_variants_bitexact(case):
     assert_bitexact(o, g)
 
 
-@pytest.mark.parametrize("n_cells,rows,kernel", [
-    (256, 1, "cols"), (257, 1, "spans"), (128, 2, "cols"), (129, 2, "spans")])
-def test_span_prefix_kernels_bitexact(n_cells, rows, kernel):
-    """The prefix of the sort matrix down its rows runs as one thread per cell walking
-    its column while an instance has at most 256 rows (spans x sort rows), else as blocks
-    of 32 cells x 32 row segments.  One-cell spans put each case on either side of the
-    threshold; every case bit-exact against the oracle over 5 steps."""
-    o, g = make_pair(Kn=1.0, n_cells=n_cells, ppc=1100, F=W.f0_force(1.0), seed=21,
+@pytest.mark.parametrize("n_cells,ppc,rows,kernel", [
+    (256, 1100, 1, "fused"), (257, 1100, 1, "spans"), (128, 1100, 2, "fused"),
+    (129, 1100, 2, "spans"), (1024, 100, 1, "fused"), (1025, 100, 1, "cols")])
+def test_span_prefix_kernels_bitexact(n_cells, ppc, rows, kernel):
+    """The prefix of the sort matrix down its rows and the new cell offsets: one launch of
+    one CTA while the run has at most 1,024 cells and 256 rows (spans x sort rows); with
+    more cells but at most 256 rows a thread per cell walking its column, then the offsets;
+    else blocks of 32 cells x 32 row segments, then the offsets.  Cases on either side of
+    each threshold (spans of 1,024 particles), bit-exact against the oracle over 5 steps."""
+    o, g = make_pair(Kn=1.0, n_cells=n_cells, ppc=ppc, F=W.f0_force(1.0), seed=21,
                      span_particles=1024, span_rows=rows)
     info = g.info()
-    assert info["n_spans"] == n_cells and info["cells_per_span"] == 1
-    assert (n_cells * rows <= 256) == (kernel == "cols")
+    n_rows = info["n_spans"] * rows
+    expect = ("fused" if n_cells <= 1024 and n_rows <= 256 else
+              "cols" if n_rows <= 256 else "spans")
+    assert expect == kernel, (info["n_spans"], n_rows)
     o.step(5)
     g.step(5)
     assert_bitexact(o, g)
