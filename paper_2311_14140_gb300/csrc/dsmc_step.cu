@@ -48,7 +48,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // sin(2 pi v) and cos(2 pi v) for v in [0, 1], binary32: 4 v = n + r with n the nearest
 // integer (4 v, n and r exact), theta = r pi/2 in [-pi/4, pi/4], the Taylor series of
 // sin theta through theta^9 and of cos theta through theta^10 (truncation below 2e-9 on
-// that range) by Horner's rule, then n quarter turns.
+// that range) by Horner's rule, then n quarter turns (selects, not branches: lanes of a
+// warp fall in different quadrants).
 __device__ __forceinline__ void sincos_turn(float v, float& sn, float& cs) {
   const float t = fmul(4.0f, v);
   const float n = floorf(fadd(t, 0.5f));
@@ -67,12 +68,10 @@ __device__ __forceinline__ void sincos_turn(float v, float& sn, float& cs) {
   pc = fadd(fmul(pc, t2), 0x1.555556p-5f);     // 1/4!
   pc = fsub(fmul(pc, t2), 0.5f);
   const float c = fadd(1.0f, fmul(t2, pc));
-  switch (((int)n) & 3) {
-    case 0: sn = s; cs = c; break;
-    case 1: sn = c; cs = -s; break;
-    case 2: sn = -s; cs = -c; break;
-    default: sn = -c; cs = s; break;
-  }
+  const int q = ((int)n) & 3;  // quarter turns: swap for odd q, signs by quadrant
+  const float a = (q & 1) ? c : s, b = (q & 1) ? s : c;
+  sn = (q & 2) ? -a : a;
+  cs = ((q + 1) & 2) ? -b : b;
 }
 
 // VHS acceptance threshold on the relative speed (sigma g > u (sigma g)_max written as
