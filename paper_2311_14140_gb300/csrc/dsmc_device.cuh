@@ -132,15 +132,21 @@ __device__ __forceinline__ float pow32(float g, float a) {
   return exp32(fmul(a, ln32(g)));
 }
 
-// One polar (Marsaglia-Bray) attempt: two N(0,1/2) deviates or a rejection.
+// The two N(0,1/2) deviates of an accepted polar (Marsaglia-Bray) attempt (a0, a1) with
+// s = a0^2 + a1^2 < 1.
+__device__ __forceinline__ void polar_scale(float a0, float a1, float s, float& z0, float& z1) {
+  const float fac = fsqrt(fdiv(-ln32(s), s));
+  z0 = fmul(a0, fac);
+  z1 = fmul(a1, fac);
+}
+
+// One polar attempt: two N(0,1/2) deviates or a rejection.
 __device__ __forceinline__ bool polar_pair(uint32_t w0, uint32_t w1, float& z0, float& z1) {
   const float a0 = s11(w0);
   const float a1 = s11(w1);
   const float s = fadd(fmul(a0, a0), fmul(a1, a1));
   if (s >= 1.0f) return false;
-  const float fac = fsqrt(fdiv(-ln32(s), s));
-  z0 = fmul(a0, fac);
-  z1 = fmul(a1, fac);
+  polar_scale(a0, a1, s, z0, z1);
   return true;
 }
 
@@ -305,15 +311,27 @@ __device__ __forceinline__ bool fly_with(float& y, float& vx, float& vy, float& 
     const uint32_t c3 = kStreamMove << 24;
     U4 w = gen(slot, c1, step, c3);
     const float speed = fsqrt(-ln32(u01(w.x)));
-    float z0 = 0.0f, z1 = 0.0f;
+    // polar attempts until one falls inside the unit disc; the logarithm, division and
+    // square root of the accepted attempt once after the loop (the lanes of a warp need
+    // different numbers of attempts, so inside it they would run once per attempt)
+    float a0 = 0.0f, a1 = 0.0f, sacc = 0.0f;
     bool got = false;
     for (int a = 0; a < kNormalAttempts && !got; ++a) {
       if ((a & 1) == 0) w = gen(slot, c1 | (1u + (uint32_t)(a >> 1)), step, c3);
-      got = (a & 1) ? polar_pair(w.z, w.w, z0, z1) : polar_pair(w.x, w.y, z0, z1);
+      const float t0 = s11((a & 1) ? w.z : w.x);
+      const float t1 = s11((a & 1) ? w.w : w.y);
+      const float sq = fadd(fmul(t0, t0), fmul(t1, t1));
+      if (sq < 1.0f) {
+        a0 = t0;
+        a1 = t1;
+        sacc = sq;
+        got = true;
+      }
     }
-    if (!got) {
-      z0 = 0.0f;
-      z1 = 0.0f;
+    float z0 = 0.0f, z1 = 0.0f;
+    if (got) {
+      polar_scale(a0, a1, sacc, z0, z1);
+    } else {
       ok = false;
     }
     vx = z0;
