@@ -284,18 +284,15 @@ __device__ __forceinline__ bool fly_with(float& y, float& vx, float& vy, float& 
   bool ok = true;
   for (int b = 0;; ++b) {
     const float ynew = fadd(y, fmul(vy, t));
-    float thit, wall;
-    if (ynew < 0.0f) {
-      thit = fdiv(y, -vy);
-      wall = 0.0f;
-    } else if (ynew > 1.0f) {
-      thit = fdiv(fsub(1.0f, y), vy);
-      wall = 1.0f;
-    } else {
+    if (!(ynew < 0.0f) && !(ynew > 1.0f)) {
       y = ynew;
       vx = fadd(vx, fmul(F, t));
       return ok;
     }
+    // time to the wall reached, one division for lanes bound for either wall
+    const bool bottom = ynew < 0.0f;
+    float thit = fdiv(bottom ? y : fsub(1.0f, y), bottom ? -vy : vy);
+    const float wall = bottom ? 0.0f : 1.0f;
     if (b >= kMaxBounces) {  // leave the particle on the wall
       y = wall;
       return false;
