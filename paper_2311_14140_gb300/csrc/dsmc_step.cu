@@ -138,7 +138,7 @@ struct LaneSums<float> {
     e = __ffma2_rn(make_float2(y, z), make_float2(z, v2), e);
     f = __ffma2_rn(xy, make_float2(v2, v2), f);
   }
-  // moment k = 1..12 of the survey's order (1 vx, 2 vy, 3 vz, 4 vx2, 5 vy2, 6 vz2,
+  // moment k = 1..12 in the order of the raw sums (1 vx, 2 vy, 3 vz, 4 vx2, 5 vy2, 6 vz2,
   // 7 vxvy, 8 vxvz, 9 vyvz, 10 vx v2, 11 vy v2, 12 vz v2); 0 for the padding slots
   __device__ __forceinline__ float get(int k) const {
     switch (k) {
