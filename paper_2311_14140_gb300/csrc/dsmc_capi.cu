@@ -345,6 +345,7 @@ struct dsmc_sim {
   int cta_warps = kAWarps;  // warps per CTA of the collide/move pass
   int span_rows = 1;        // sort-matrix rows per span
   int spans = 0, max_cps = 1, max_cells = 1, max_spans = 1;  // partition in use
+  long long part_total = 0;  // particles of the active instances
   int spans_reserved = 0;
   Capacity C{};
   Layout L{};
@@ -489,8 +490,10 @@ void set_partition(dsmc_sim* h, int target) {
   h->span_target = target;
   h->span_inst.clear();
   int base = 0, m = 1, mc = 1, ms = 1;
+  long long np = 0;
   for (int t = 0; t < h->n_inst(); ++t) {
     Inst& x = h->inst[h->order[t]];
+    np += x.N;
     make_spans(x.n_cells, x.ppc, target, &x.cps, &x.n_spans);
     x.span_base = base;
     base += x.n_spans;
@@ -503,6 +506,7 @@ void set_partition(dsmc_sim* h, int target) {
   h->max_cps = m;
   h->max_cells = mc;
   h->max_spans = ms;
+  h->part_total = np;
   set_span_order(h);
   h->tab_dirty = h->spans_dirty = true;
   h->graph_valid = false;
@@ -589,6 +593,7 @@ StepLaunch step_launch(const dsmc_sim* h, bool count_only) {
   L.n_spans_total = h->spans;
   L.max_cells = h->max_cells;
   L.max_spans = h->max_spans;
+  L.n_part_total = h->part_total;
   L.max_cps = h->max_cps;
   L.max_cap = h->cap();
   L.warps = h->cta_warps;
@@ -666,8 +671,10 @@ dsmc_status admit_fresh(dsmc_sim* h) {
   h->adm_tab.clear();
   h->adm_span.clear();
   int base = 0, m = 1, mc = 1, ms = 1;
+  long long np = 0;
   for (size_t k = 0; k < ids.size(); ++k) {
     const Inst& x = h->inst[ids[k]];
+    np += x.N;
     h->adm_tab.push_back(instance_params(h, ids[k], base));
     h->adm_span.insert(h->adm_span.end(), (size_t)x.n_spans, (int)k);
     base += x.n_spans;
@@ -699,6 +706,7 @@ dsmc_status admit_fresh(dsmc_sim* h) {
   SL.n_spans_total = base;
   SL.max_cells = mc;
   SL.max_spans = ms;
+  SL.n_part_total = np;
   SL.max_cps = m;
   SL.max_cap = h->cap();
   SL.warps = h->cta_warps;

@@ -182,6 +182,7 @@ struct StepLaunch {
   int n_spans_total;
   int max_cells;         // largest n_cells of the instances
   int max_spans;         // largest n_spans of the instances
+  long long n_part_total;  // particles of all the launch's instances
   int max_cps;
   int max_cap;
   int warps;             // warps per CTA of the collide/move pass (kAWarps or kAWarpsSmall)

@@ -833,11 +833,13 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
 }
 
 // One CTA of kCoopWarps warps per (span, row): the stable scatter of the row's records
-// into the other buffer, kCoopWarps * 32 records per round.  In a round warp w takes the
-// 32 consecutive records [base + 32 w, base + 32 w + 32); a record's place is
+// into the other buffer, kCoopWarps * 64 records per round.  In a round warp w takes the
+// 64 consecutive records [base + 64 w, base + 64 w + 64) as two 32-record slices; a
+// record's place is
 //   run[cell]                      the cell's next slot after the earlier rounds,
 // + sum over warps w' < w of       the round's records of w' bound for the same cell,
-// + its rank among the lanes of its own warp bound for the same cell (__match_any_sync).
+// + its rank among its warp's records bound for the same cell (__match_any_sync within
+//   its slice, plus the first slice's count for a record of the second).
 // Each warp publishes its per-cell counts in its own row of a table tagged with the
 // round number (no clearing between rounds); after the places are taken, every warp
 // adds its counts into run[].  All warps of the CTA work on one span at once: for
@@ -848,7 +850,7 @@ __global__ void __launch_bounds__(kBWarpsMax * 32)
 constexpr int kCoopWarps = 8;
 constexpr size_t kCoopSmemMax = 48 * 1024;
 
-template <bool kBatch>
+template <bool kBatch, int kSlices>
 __global__ void __launch_bounds__(kCoopWarps * 32)
     k_scatter_coop(const float4* __restrict__ P, float4* __restrict__ P2,
                    const int* __restrict__ off_cur_all, const int* __restrict__ off_new_all,
@@ -877,15 +879,22 @@ __global__ void __launch_bounds__(kCoopWarps * 32)
   const int b1 = (sub == 0) ? mid : sb1;
   const int lo = a.part_base, hi = a.part_base + a.n_part;  // the instance's slots
   const unsigned lt = (1u << lane) - 1u;
-  constexpr int kRound = kCoopWarps * 32;
-  constexpr int kAhead = 6;  // rounds of records in flight per lane
-  float4 r[kAhead];
+  // A round: warp w takes the 32 kSlices records [base + 32 kSlices w, ...) as kSlices
+  // slices of 32 (one record per lane each); two barriers per round.
+  static_assert(kSlices == 1 || kSlices == 2, "one or two slices per warp and round");
+  constexpr int kWarpRecs = 32 * kSlices;
+  constexpr int kRound = kCoopWarps * kWarpRecs;
+  constexpr int kAhead = 6 / kSlices;  // rounds of records in flight per lane (6 records)
+  float4 r[kAhead][kSlices];
 #pragma unroll
-  for (int u = 0; u < kAhead; ++u) {
-    const int p = b0 + u * kRound + w * 32 + lane;
-    if (p < b1) r[u] = P[p];
-  }
+  for (int u = 0; u < kAhead; ++u)
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl) {
+      const int p = b0 + u * kRound + w * kWarpRecs + sl * 32 + lane;
+      if (p < b1) r[u][sl] = P[p];
+    }
   bool bad = false;
+  int* tw = tab + w * n_cells;  // this warp's counts of the round, per cell
   __syncthreads();
   int round = 0;
   for (int base = b0; base < b1; base += kAhead * kRound) {
@@ -893,20 +902,39 @@ __global__ void __launch_bounds__(kCoopWarps * 32)
     for (int u = 0; u < kAhead; ++u, ++round) {
       const int rb = base + u * kRound;
       if (rb >= b1) break;  // uniform across the CTA
-      const int p = rb + w * 32 + lane;
-      const bool act = p < b1;
-      const float4 rec = r[u];
-      // the record kAhead rounds later into this register
-      const int pn = p + kAhead * kRound;
-      if (pn < b1) r[u] = P[pn];
-      const int cell = act ? cell_of(rec.x, n_cells, a.ncf) : -1;
-      const unsigned peers = __match_any_sync(kFull, cell);
-      const bool leader = act && (peers & lt) == 0u;
-      const int nw = __popc(peers);
-      if (leader) tab[w * n_cells + cell] = (round << 8) | nw;
+      const int p0 = rb + w * kWarpRecs + lane, p1 = p0 + 32;
+      const bool act0 = p0 < b1, act1 = kSlices > 1 && p1 < b1;
+      const float4 rec0 = r[u][0], rec1 = r[u][kSlices - 1];
+      // the records kAhead rounds later into these registers
+      if (p0 + kAhead * kRound < b1) r[u][0] = P[p0 + kAhead * kRound];
+      if (kSlices > 1 && p1 + kAhead * kRound < b1) r[u][kSlices - 1] = P[p1 + kAhead * kRound];
+      const int cell0 = act0 ? cell_of(rec0.x, n_cells, a.ncf) : -1;
+      const unsigned peers0 = __match_any_sync(kFull, cell0);
+      const bool lead0 = act0 && (peers0 & lt) == 0u;
+      const int nw0 = __popc(peers0);
+      const int tag = round << 8;
+      if (lead0) tw[cell0] = tag | nw0;
+      int cell1 = -1, nw1 = 0, in0 = 0;
+      unsigned peers1 = 0u;
+      bool lead1 = false;
+      if constexpr (kSlices > 1) {
+        // the second slice's lanes find how many of the first slice precede them in their
+        // cell and complete the warp's count per cell
+        cell1 = act1 ? cell_of(rec1.x, n_cells, a.ncf) : -1;
+        peers1 = __match_any_sync(kFull, cell1);
+        lead1 = act1 && (peers1 & lt) == 0u;
+        nw1 = __popc(peers1);
+        __syncwarp();
+        if (act1) {
+          const int e = tw[cell1];
+          in0 = ((e >> 8) == round) ? (e & 0xff) : 0;
+        }
+        __syncwarp();
+        if (lead1) tw[cell1] = tag | (in0 + nw1);
+      }
       __syncthreads();
-      if (act) {
-        int before = __popc(peers & lt);
+      auto place = [&](bool act, int cell, int before, const float4& rec) {
+        if (!act) return;
 #pragma unroll
         for (int v = 0; v < kCoopWarps - 1; ++v) {
           if (v < w) {
@@ -919,9 +947,13 @@ __global__ void __launch_bounds__(kCoopWarps * 32)
           P2[d] = rec;
         else
           bad = true;
-      }
+      };
+      place(act0, cell0, __popc(peers0 & lt), rec0);
+      if constexpr (kSlices > 1) place(act1, cell1, in0 + __popc(peers1 & lt), rec1);
       __syncthreads();
-      if (leader) atomicAdd(&run[cell], nw);
+      if (lead0) atomicAdd(&run[cell0], nw0);
+      if constexpr (kSlices > 1)
+        if (lead1) atomicAdd(&run[cell1], nw1);
     }
   }
   if (bad) atomicOr(err, kErrSort);
@@ -1264,12 +1296,19 @@ cudaError_t launch_scatter_spans(const float4* P, float4* P2, const int* off_cur
   const size_t coop = scatter_coop_smem(L.max_cells);
   if (coop <= kCoopSmemMax) {  // a CTA per (span, row)
     const int units = L.n_spans_total * L.rows;
-    if (L.n_inst == 1)
-      k_scatter_coop<false><<<units, kCoopWarps * 32, coop, st>>>(P, P2, off_cur, off_new, hist,
-                                                                   one, L, err);
-    else
-      k_scatter_coop<true><<<units, kCoopWarps * 32, coop, st>>>(P, P2, off_cur, off_new, hist,
-                                                                  one, L, err);
+    // two slices per warp and round once the rows average 4,096 records (the batch's
+    // tuned spans: 0.328 -> 0.30 ms); one for shorter rows (small runs' 1,024-particle
+    // spans, where fewer, longer rounds were slower)
+    const bool two = L.n_part_total >= 4096LL * units;
+#define DSMC_COOP(B, S)                                                                  \
+  k_scatter_coop<B, S><<<units, kCoopWarps * 32, coop, st>>>(P, P2, off_cur, off_new, hist, \
+                                                             one, L, err)
+    if (L.n_inst == 1) {
+      if (two) DSMC_COOP(false, 2); else DSMC_COOP(false, 1);
+    } else {
+      if (two) DSMC_COOP(true, 2); else DSMC_COOP(true, 1);
+    }
+#undef DSMC_COOP
     return cudaGetLastError();
   }
   const int wpb = scatter_spans_warps(L.max_cells);
@@ -1373,12 +1412,14 @@ cudaError_t set_step_smem_limits(size_t a_bytes, size_t b_bytes) {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a_bytes);
     if (e != cudaSuccess) return e;
   }
-  const void* scatter[6] = {(const void*)k_scatter_spans<false, false>,
+  const void* scatter[8] = {(const void*)k_scatter_spans<false, false>,
                             (const void*)k_scatter_spans<false, true>,
                             (const void*)k_scatter_spans<true, false>,
                             (const void*)k_scatter_spans<true, true>,
-                            (const void*)k_scatter_coop<false>,
-                            (const void*)k_scatter_coop<true>};
+                            (const void*)k_scatter_coop<false, 1>,
+                            (const void*)k_scatter_coop<true, 1>,
+                            (const void*)k_scatter_coop<false, 2>,
+                            (const void*)k_scatter_coop<true, 2>};
   for (const void* f : scatter) {
     const cudaError_t e =
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_bytes);

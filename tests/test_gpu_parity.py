@@ -126,6 +126,8 @@ def test_vhs_kn01_multigroup_deterministic(warps, rows):
     # the same with two sort rows per span (a CTA per row)
     dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=1024, span_rows=2,
          spans=1000),
+    # rows of ~8,400 records: two 32-record slices per warp and round
+    dict(Kn=0.1, omega=0.81, n_cells=1000, ppc=1200, span_particles=8192, spans=143),
     # more cells, a warp per span: 750 spans, the mask table
     dict(Kn=0.1, omega=0.81, n_cells=1500, ppc=800, span_particles=1024, spans=750),
     # the same run in 137 spans: __match_any_sync
@@ -139,8 +141,9 @@ def test_vhs_kn01_multigroup_deterministic(warps, rows):
 ])
 def test_scatter_variants_bitexact(case):
     """The stable scatter runs a CTA per span while its shared memory (nine words per
-    cell) leaves room for 4 CTAs per SM (up to 1,365 cells); above, a warp per span,
-    which ranks same-cell records with a shared-memory mask table when at least four of
+    cell) leaves room for 4 CTAs per SM (up to 1,365 cells), its warps taking one or, for
+    rows averaging 4,096 records or more, two 32-record slices per round; above, a warp
+    per span, which ranks same-cell records with a shared-memory mask table when at least four of
     its warps (spans) share an SM (a 152-SM GPU: 608 spans), else with
     __match_any_sync, and falls back to __match_any_sync for a slice whose cells span
     256 values or more.  Each case bit-exact against the oracle over 6 steps."""
