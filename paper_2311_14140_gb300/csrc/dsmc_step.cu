@@ -902,58 +902,58 @@ __global__ void __launch_bounds__(kCoopWarps * 32)
     for (int u = 0; u < kAhead; ++u, ++round) {
       const int rb = base + u * kRound;
       if (rb >= b1) break;  // uniform across the CTA
-      const int p0 = rb + w * kWarpRecs + lane, p1 = p0 + 32;
-      const bool act0 = p0 < b1, act1 = kSlices > 1 && p1 < b1;
-      const float4 rec0 = r[u][0], rec1 = r[u][kSlices - 1];
-      // the records kAhead rounds later into these registers
-      if (p0 + kAhead * kRound < b1) r[u][0] = P[p0 + kAhead * kRound];
-      if (kSlices > 1 && p1 + kAhead * kRound < b1) r[u][kSlices - 1] = P[p1 + kAhead * kRound];
-      const int cell0 = act0 ? cell_of(rec0.x, n_cells, a.ncf) : -1;
-      const unsigned peers0 = __match_any_sync(kFull, cell0);
-      const bool lead0 = act0 && (peers0 & lt) == 0u;
-      const int nw0 = __popc(peers0);
+      const int pw = rb + w * kWarpRecs + lane;
+      float4 rec[kSlices];
+      int cell[kSlices], prev[kSlices];
+      unsigned peers[kSlices];
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        const int p = pw + 32 * sl;
+        rec[sl] = r[u][sl];
+        // the record kAhead rounds later into this register
+        if (p + kAhead * kRound < b1) r[u][sl] = P[p + kAhead * kRound];
+        cell[sl] = (p < b1) ? cell_of(rec[sl].x, n_cells, a.ncf) : -1;
+        peers[sl] = __match_any_sync(kFull, cell[sl]);
+      }
       const int tag = round << 8;
-      if (lead0) tw[cell0] = tag | nw0;
-      int cell1 = -1, nw1 = 0, in0 = 0;
-      unsigned peers1 = 0u;
-      bool lead1 = false;
-      if constexpr (kSlices > 1) {
-        // the second slice's lanes find how many of the first slice precede them in their
-        // cell and complete the warp's count per cell
-        cell1 = act1 ? cell_of(rec1.x, n_cells, a.ncf) : -1;
-        peers1 = __match_any_sync(kFull, cell1);
-        lead1 = act1 && (peers1 & lt) == 0u;
-        nw1 = __popc(peers1);
-        __syncwarp();
-        if (act1) {
-          const int e = tw[cell1];
-          in0 = ((e >> 8) == round) ? (e & 0xff) : 0;
+      // the warp's count per cell, slice after slice: a slice's lanes find how many of the
+      // earlier slices precede them in their cell, and its leaders store the running count
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        prev[sl] = 0;
+        if (sl > 0) {
+          __syncwarp();
+          if (cell[sl] >= 0) {
+            const int e = tw[cell[sl]];
+            prev[sl] = ((e >> 8) == round) ? (e & 0xff) : 0;
+          }
+          __syncwarp();
         }
-        __syncwarp();
-        if (lead1) tw[cell1] = tag | (in0 + nw1);
+        if (cell[sl] >= 0 && (peers[sl] & lt) == 0u)
+          tw[cell[sl]] = tag | (prev[sl] + __popc(peers[sl]));
       }
       __syncthreads();
-      auto place = [&](bool act, int cell, int before, const float4& rec) {
-        if (!act) return;
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        if (cell[sl] < 0) continue;
+        int before = prev[sl] + __popc(peers[sl] & lt);
 #pragma unroll
         for (int v = 0; v < kCoopWarps - 1; ++v) {
           if (v < w) {
-            const int e = tab[v * n_cells + cell];
+            const int e = tab[v * n_cells + cell[sl]];
             if ((e >> 8) == round) before += e & 0xff;
           }
         }
-        const int d = run[cell] + before;
+        const int d = run[cell[sl]] + before;
         if (d >= lo && d < hi)
-          P2[d] = rec;
+          P2[d] = rec[sl];
         else
           bad = true;
-      };
-      place(act0, cell0, __popc(peers0 & lt), rec0);
-      if constexpr (kSlices > 1) place(act1, cell1, in0 + __popc(peers1 & lt), rec1);
+      }
       __syncthreads();
-      if (lead0) atomicAdd(&run[cell0], nw0);
-      if constexpr (kSlices > 1)
-        if (lead1) atomicAdd(&run[cell1], nw1);
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl)
+        if (cell[sl] >= 0 && (peers[sl] & lt) == 0u) atomicAdd(&run[cell[sl]], __popc(peers[sl]));
     }
   }
   if (bad) atomicOr(err, kErrSort);
