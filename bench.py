@@ -91,13 +91,22 @@ def ncu_traffic(kernel: str):
 STEP_SOURCES = ("dsmc_step.cu", "dsmc_device.cuh", "dsmc_internal.h")
 
 
+def _code_only(text: str) -> str:
+    """The source without its comments and trailing blanks (so a reworded comment does not
+    void a traffic record of unchanged kernels)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_14140_gb300", "csrc")
     for fn in STEP_SOURCES:
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(fn.encode() + b"\0" + f.read())
+        with open(os.path.join(csrc, fn), encoding="utf-8") as f:
+            h.update(fn.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()
 
 

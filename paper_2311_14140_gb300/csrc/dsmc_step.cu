@@ -29,10 +29,11 @@
 //                    and scatters it stably into the other buffer from the span's row of
 //                    the prefix-summed matrix plus the new cell offsets.
 //   k_scatter_coop   the same scatter with a CTA per span (up to 1,365 cells): all its
-//                    warps rank one round of 256 records at a time.
+//                    warps rank one round of 256 (or 512) records at a time.
 //
 // Between them, k_scan_spans (or k_scan_cols for instances of few spans) and
-// k_offsets_cells (below) turn the matrix into per-span bases and the new cell offsets.
+// k_offsets_cells (below) turn the matrix into per-span bases and the new cell offsets;
+// for a small single run k_prefix_small does both in one launch.
 #include <climits>
 #include <type_traits>
 
